@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the two-component Shan-Chen D2Q9 step with the
+improved virtual-density wetting condition on one GB300.
+
+Workload: 8192 x 8192 fully periodic porous medium of non-overlapping disks
+(radius uniform in [8, 40], solid fraction 0.40, seed 1) with sharp droplets
+of the majority component (radius uniform in [8, 32]) filling 30% of the
+pore space (seed 2); G_AB = 3, tau = 1, improved virtual-density scheme with
+xi = -0.2. One bench step is one time step over the whole grid. The metric
+is MLUPS counted over fluid nodes.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. With --gpus N (under torchrun) every rank runs an
+independent replica on its own GPU (the method has no exchange between
+independent simulations): value = all ranks' fluid-node updates / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % HBM roofline at 1 GB300 (FP32 vs FP16-storage vs batched), err vs FP64"
+BYTES_PER_UPDATE = {"fp32": 144, "fp64": 288, "fp16": 72, "bf16": 72}
+XI = -0.2  # the paper's coalescence runs (theta = 71 deg)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def chi_from_xi(xi):
+    """chi of Eq. 8 as passed to the library for the paper's xi: the paper's
+    convention (xi < 0 hydrophilic) with the force of Eq. 7 taken as
+    printed corresponds to chi^A = 1 - xi, chi^B = 1 + xi."""
+    return (1.0 - xi, 1.0 + xi)
+
+
+def workload(n, cache=True):
+    from paper_2009_12584_gb300 import inputs
+    path = os.path.join(tempfile.gettempdir(), f"lbm_porous_{n}_v1.npz")
+    if cache and os.path.exists(path):
+        d = np.load(path)
+        return d["mask"], d["rA"], d["rB"]
+    t0 = time.time()
+    mask = inputs.porous_disks(n, n, solid_fraction=0.40, rmin=8, rmax=40, seed=1)
+    rA, rB = inputs.pore_droplets(mask, a_fraction=0.30, rmin=8, rmax=32, seed=2)
+    log(f"[bench] generated {n}^2 porous workload in {time.time() - t0:.1f}s")
+    if cache:
+        try:
+            np.savez(path, mask=mask, rA=rA, rB=rB)
+        except OSError:
+            pass
+    return mask, rA, rB
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2009_12584_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel_class, storage):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    e = d.get(f"{kernel_class}/{storage}")
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("bytes_per_launch_full")
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        rows = []
+        for line in open(self.out.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), max=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.out.name)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                            ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[k].lower() == "active":
+                    reasons.add(name)
+        sm = sorted(r["sm"] for r in rows)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r["max"] for r in rows),
+                "power_w_max": max(r["power"] for r in rows), "samples": len(rows),
+                "reasons": sorted(reasons)}
+
+
+def cpu_baseline(target_s=15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: a
+    512 x 512 periodic porous medium drawn with the same recipe."""
+    import oracle
+    from paper_2009_12584_gb300 import inputs
+    n = 512
+    mask = inputs.porous_disks(n, n, solid_fraction=0.40, rmin=8, rmax=40, seed=1)
+    rA, rB = inputs.pore_droplets(mask, a_fraction=0.30, rmin=8, rmax=32, seed=2)
+    o = oracle.Oracle(n, n, mask, periodic_x=True, periodic_y=True, bc=oracle.BC_VIRTUAL_AVG,
+                      G_s=(3.0, 3.0), chi=chi_from_xi(XI)).init(rA, rB)
+    t0 = time.perf_counter()
+    o.step(1)
+    per = time.perf_counter() - t0
+    steps = max(2, int(target_s / max(per, 1e-3)))
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    nf = int((mask == 0).sum())
+    return {"value": nf * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{n}x{n} periodic porous medium (same recipe, seeds 1/2), improved BC, FP64, "
+                      f"{steps} steps, {dt:.1f} s, single thread"}
+
+
+def run_reference(args, rank):
+    """Reference arm: the FP64 oracle timed on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2009_12584_gb300 import inputs
+    probe = 128
+    m = inputs.porous_disks(probe, probe, 0.40, 8, 40, seed=1)
+    a, b = inputs.pore_droplets(m, 0.30, 8, 32, seed=2)
+    o = oracle.Oracle(probe, probe, m, periodic_x=True, periodic_y=True, bc=oracle.BC_VIRTUAL_AVG,
+                      G_s=(3.0, 3.0), chi=chi_from_xi(XI)).init(a, b)
+    t0 = time.perf_counter()
+    o.step(2)
+    rate = probe * probe * 2 / (time.perf_counter() - t0)
+    budget = 120.0
+    side = int(np.sqrt(budget * rate / max(1, args.steps + args.warmup)))
+    side = int(max(64, min(1024, side)))
+    mask = inputs.porous_disks(side, side, 0.40, 8, 40, seed=1)
+    rA, rB = inputs.pore_droplets(mask, 0.30, 8, 32, seed=2)
+    o = oracle.Oracle(side, side, mask, periodic_x=True, periodic_y=True, bc=oracle.BC_VIRTUAL_AVG,
+                      G_s=(3.0, 3.0), chi=chi_from_xi(XI)).init(rA, rB)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    nf = int((mask == 0).sum())
+    v = nf * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"porous medium {side}x{side} sample of the 8192x8192 recipe",
+                       "nx": side, "ny": side, "fluid_nodes": nf, "bc": "virtual_avg", "storage": "fp64"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{side}x{side} porous medium, same recipe, {args.steps} steps"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "two_pass", "fused"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2009_12584_gb300 import build, lbm
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+
+    n = args.n
+    mask, rA, rB = workload(n)
+    nf = int((mask == 0).sum())
+    chi = chi_from_xi(XI)
+    sim = lbm.Simulation(n, n, periodic_x=True, periodic_y=True, storage=args.storage, kernel=args.kernel)
+    sim.set_geometry(mask).set_wetting("virtual_avg", G_s=(3.0, 3.0), chi=chi).init_fields(rA, rB)
+    stream = torch.cuda.current_stream()
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip()]
+    sampler = ClockSampler(ids[local] if local < len(ids) else local)
+    sampler.start()
+    time.sleep(0.4)
+    l0 = sim.launch_count
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ms_cls, cnt_cls = sim.step_profiled(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = sim.launch_count - l0
+    clocks = sampler.stop()
+    t_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = t_ms / args.steps
+    value = world * nf * args.steps / (t_ms / 1e3) / 1e6
+
+    # dominant kernel and its roofline
+    dom = max(ms_cls, key=lambda k: ms_cls[k])
+    per_launch_ms = ms_cls[dom] / max(1, cnt_cls[dom])
+    bpu = BYTES_PER_UPDATE[args.storage] if dom in ("fused", "collide") else BYTES_PER_UPDATE[args.storage] // 2
+    alg_bytes = bpu * nf
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    pk, pk_kind = peaks()
+    traffic = measured_traffic(dom, args.storage)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
+                "peak_kind": pk_kind, "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
+                "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
+                "per_launch_ms": round(per_launch_ms, 4),
+                "kernel_ms_per_step": {k: round(v / args.steps, 4) for k, v in ms_cls.items() if cnt_cls[k]}}
+
+    # end to end through the host API: host buffers in, host buffers out
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h_mask, h_rA, h_rB = pin(mask), pin(rA), pin(rB)
+        outs = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(4)]
+        sim2 = sim  # reuse the context and its workspace
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim2.run_host(sim.wetting, h_mask, h_rA, h_rB, args.steps, outs)
+        t_e2e = time.perf_counter() - t0
+        h2d = mask.nbytes + rA.nbytes + rB.nbytes
+        d2h = sum(o.numel() * 8 for o in outs)
+        e2e = {"value": nf * args.steps / t_e2e / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "wall_s": round(t_e2e, 3),
+               "what": "lbm_run_host: mask+densities H2D, geometry, init, K steps, moments D2H"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f32 (fp16 storage)",
+                          "bf16": "f32 (bf16 storage)"}[args.storage],
+                "data": "synthetic",
+                "config": {"workload": f"porous medium {n}x{n}, improved virtual-density BC, {args.storage}",
+                           "nx": n, "ny": n, "fluid_nodes": nf, "solid_fraction": round(1 - nf / n / n, 4),
+                           "bc": "virtual_avg", "xi": XI, "chi": chi, "tau": 1.0, "G_AB": 3.0,
+                           "storage": args.storage, "kernel": args.kernel,
+                           "l2": "inputs larger than L2 (populations %.1f GB per buffer)"
+                                 % (18 * n * n * BYTES_PER_UPDATE[args.storage] / 144 * 4 / 1e9),
+                           "all_node_mlups": round(world * n * n * args.steps / (t_ms / 1e3) / 1e6, 1),
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,225 @@
+/*
+ * lbm.h - C ABI of the GB300 library for the two-component Shan-Chen
+ * pseudopotential lattice Boltzmann step on D2Q9 with wetting boundary
+ * conditions (Coelho, Moura, Telo da Gama, Araujo, "Wetting boundary
+ * conditions for multicomponent pseudopotential lattice Boltzmann",
+ * arXiv:2009.12584).
+ *
+ * One time step (lbm_step) computes, for both components A and B:
+ *   - the densities rho^sigma = sum_i f_i^sigma and pseudopotentials
+ *     psi = rho (Eq. 3, Eq. 5),
+ *   - the virtual solid densities of the improved scheme at interface-solid
+ *     nodes (Eq. 8, D2Q25 weights),
+ *   - the Shan-Chen force summed over fluid neighbours (Eq. 5) plus the
+ *     adhesion force (Eq. 7) of the selected wetting scheme,
+ *   - the common velocity u^eq (Eq. 3), BGK collision towards Eq. 2 with the
+ *     Guo source of Eq. 4, streaming and halfway bounce-back (Eq. 1, Sec. 2).
+ *
+ * Conventions shared by every entry point
+ *   - Grids are nx * ny nodes, row-major, node (x, y) at index y*nx + x.
+ *     Component 0 is A (the droplet fluid), 1 is B. D2Q9 directions:
+ *     0 rest, 1 (1,0), 2 (0,1), 3 (-1,0), 4 (0,-1), 5 (1,1), 6 (-1,1),
+ *     7 (-1,-1), 8 (1,-1).
+ *   - "d_" pointers are device pointers the caller owns (e.g. torch tensor
+ *     storage); "h_" pointers are host pointers. The library never frees
+ *     caller memory and allocates no device memory of its own: every device
+ *     buffer lives in the caller-provided workspace. The context object
+ *     itself is a small host allocation released by lbm_destroy.
+ *   - All device work is enqueued on the context's stream (a cudaStream_t
+ *     passed as void*; NULL is the legacy default stream). Calls return when
+ *     the work is enqueued, except where a call says it synchronises.
+ *   - Every call returns an lbm_status; no call aborts, throws or exits. A
+ *     CUDA error is returned as LBM_ERR_CUDA and its text is kept in the
+ *     context (lbm_last_error). An asynchronous kernel fault surfaces at the
+ *     next call that synchronises.
+ *   - Masks: 1 = solid (phi = 1), 0 = fluid (Sec. 2). On a non-periodic axis
+ *     the first and last row/column must be solid (the paper's walls on the
+ *     box borders, Sec. 3.1); lbm_set_geometry rejects masks with fluid
+ *     there.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = 1,     /* invalid argument (null pointer, size, range) */
+  LBM_ERR_STATE = 2,   /* call out of order (e.g. step before geometry) */
+  LBM_ERR_CUDA = 3,    /* CUDA runtime error; see lbm_last_error */
+  LBM_ERR_SPACE = 4,   /* workspace too small for the request */
+  LBM_ERR_TIMEOUT = 5  /* a bounded device-side wait gave up */
+} lbm_status;
+
+/* Wetting boundary conditions compared in Sec. 2 / Sec. 3. */
+typedef enum {
+  LBM_WET_MARTYS_CHEN = 0, /* S^sigma = phi; strength G_sigma,s (Eq. 7) */
+  LBM_WET_LLKC = 1,        /* S^sigma(x+c_i) = phi(x+c_i) rho^sigma(x) */
+  LBM_WET_VIRTUAL_AVG = 2, /* improved scheme: S^sigma = phi rho~^sigma, Eq. 8 */
+  LBM_WET_CONSTANT = 3     /* Chen et al.: S^sigma = phi rho_s^sigma */
+} lbm_wetting;
+
+/* Which component's solid pseudopotential enters Eq. 7 for the force on
+ * sigma. CROSS follows Eq. 7 as printed (S of sigma-bar); SELF uses S of
+ * sigma itself, the other reading found in the literature. */
+typedef enum { LBM_PAIR_CROSS = 0, LBM_PAIR_SELF = 1 } lbm_pairing;
+
+/* Storage type of the populations. Arithmetic is FP32 for FP32/FP16/BF16
+ * and FP64 for FP64. FP16/BF16 store each population as a deviation from
+ * w_i times a per-component reference density (see lbm_params). */
+typedef enum {
+  LBM_STORE_FP32 = 0,
+  LBM_STORE_FP64 = 1,
+  LBM_STORE_FP16 = 2,
+  LBM_STORE_BF16 = 3
+} lbm_storage;
+
+/* Kernel schedule for lbm_step. TWO_PASS: a density pass, the virtual
+ * density pass, then one fused force+collide+stream pull kernel. FUSED: one
+ * kernel per step that recomputes densities from the populations of a
+ * row window in shared memory (no density array in HBM). AUTO picks FUSED. */
+typedef enum {
+  LBM_KERNEL_AUTO = 0,
+  LBM_KERNEL_TWO_PASS = 1,
+  LBM_KERNEL_FUSED = 2
+} lbm_kernel;
+
+typedef struct {
+  int32_t nx, ny;             /* grid size, each >= 4 */
+  int32_t periodic_x;         /* 1: periodic along x; 0: walls */
+  int32_t periodic_y;         /* 1: periodic along y; 0: walls */
+  double tau[2];              /* BGK relaxation times, > 0.5 (Eq. 1) */
+  double G_AB;                /* Shan-Chen strength G_AB = G_BA (Eq. 5) */
+  int32_t storage;            /* lbm_storage */
+  int32_t kernel;             /* lbm_kernel */
+  double rho_ref[2];          /* FP16/BF16 reference densities (0 -> 1.0) */
+  int64_t max_interface;      /* capacity of the interface-solid list;
+                                 0 -> nx*ny (always enough) */
+} lbm_params;
+
+typedef struct {
+  int32_t kind;               /* lbm_wetting */
+  int32_t pairing;            /* lbm_pairing */
+  int32_t avg_stencil;        /* Eq. 8 weights: 25 (D2Q25, the paper's
+                                 choice) or 9 (D2Q9 variant) */
+  int32_t reserved;
+  double G_s[2];              /* G_As, G_Bs of Eq. 7. Martys-Chen and LLKC
+                                 in the paper: G_As = -G_Bs = G_w (Sec. 3.1);
+                                 virtual densities: G_As = G_Bs = G_AB */
+  double chi[2];              /* chi^A, chi^B of Eq. 8 (VIRTUAL_AVG) */
+  double rho_s[2];            /* rho_s^A, rho_s^B (CONSTANT) */
+} lbm_wetting_params;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Bytes of device workspace a context with these parameters needs.
+ * Returns LBM_ERR_ARG for invalid parameters (nx or ny < 4, tau <= 0.5,
+ * unknown storage/kernel, a grid whose index space exceeds 2^31). */
+lbm_status lbm_workspace_bytes(const lbm_params* params, size_t* bytes);
+
+/* Create a context on the caller's workspace (device memory of at least
+ * lbm_workspace_bytes, 256-byte aligned, owned by the caller and kept alive
+ * until lbm_destroy) and stream. Enqueues a clear of the workspace. */
+lbm_status lbm_create(const lbm_params* params, void* d_workspace, size_t bytes,
+                      void* cuda_stream, lbm_ctx** out);
+
+/* Replace the stream later work is enqueued on. */
+lbm_status lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
+
+/* Install the solid mask d_mask (uint8 [ny][nx], 1 = solid, device).
+ * Builds the per-node neighbour flags and the list of interface-solid nodes
+ * (solid nodes with a fluid D2Q9 neighbour, Sec. 2 last paragraph; done
+ * once, Sec. 3.2). Synchronises. LBM_ERR_ARG if a fluid node lies on a
+ * non-periodic border; LBM_ERR_SPACE if the interface list exceeds
+ * max_interface. Invalidates the populations (call lbm_init_fields). */
+lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* d_mask);
+
+/* Select the wetting scheme and its parameters (Sec. 2). LBM_ERR_ARG for an
+ * unknown kind/pairing, avg_stencil not 9 or 25, or chi outside (0, 2]. */
+lbm_status lbm_set_wetting(lbm_ctx* ctx, const lbm_wetting_params* w);
+
+/* Initialise the populations to the equilibrium of Eq. 2 with the given
+ * densities and velocity (double [ny][nx] device arrays; d_ux/d_uy may be
+ * NULL for u = 0). Solid nodes are ignored. Requires lbm_set_geometry. */
+lbm_status lbm_init_fields(lbm_ctx* ctx, const double* d_rhoA, const double* d_rhoB,
+                           const double* d_ux, const double* d_uy);
+
+/* Advance nsteps time steps (Eq. 1). Requires geometry and fields. */
+lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps);
+
+/* Kernel classes reported by lbm_step_profiled. */
+enum {
+  LBM_KC_DENSITY = 0, /* two-pass density pass */
+  LBM_KC_VIRTUAL = 1, /* virtual solid densities of Eq. 8 */
+  LBM_KC_COLLIDE = 2, /* two-pass force + collide + stream */
+  LBM_KC_FUSED = 3,   /* single-pass step */
+  LBM_KC_COUNT = 4
+};
+
+/* lbm_step with a CUDA event recorded on the context's stream around every
+ * kernel launch. Writes the summed device time per kernel class to
+ * h_ms[LBM_KC_COUNT] and the launch counts to h_launches[LBM_KC_COUNT]
+ * (host arrays; either may be NULL). Synchronises. */
+lbm_status lbm_step_profiled(lbm_ctx* ctx, int32_t nsteps, double* h_ms, int64_t* h_launches);
+
+/* Current densities and common velocity u^eq of Eq. 3 (which includes half
+ * the force) as double [ny][nx] device arrays; any pointer may be NULL.
+ * Solid nodes get 0 (rho~ is not reported). */
+lbm_status lbm_moments(lbm_ctx* ctx, double* d_rhoA, double* d_rhoB, double* d_ux,
+                       double* d_uy);
+
+/* Interaction force F^sigma (Eq. 5 + Eq. 7) of the current state: double
+ * [2 components][2 axes][ny][nx] device array, 0 at solid nodes. */
+lbm_status lbm_forces(lbm_ctx* ctx, double* d_F);
+
+/* Post-streaming populations f_i^sigma(x, t) (the left-hand side of Eq. 1)
+ * as double [2][9][ny][nx] device array, 0 at solid nodes. */
+lbm_status lbm_get_populations(lbm_ctx* ctx, double* d_f);
+
+/* Overwrite the state with post-streaming populations in the layout of
+ * lbm_get_populations (checkpoint restore). Requires lbm_set_geometry. */
+lbm_status lbm_set_populations(lbm_ctx* ctx, const double* d_f);
+
+/* Total mass of each component, sum over fluid nodes of rho^sigma,
+ * accumulated in FP64 in a fixed order (deterministic). Synchronises and
+ * writes h_out[2] on the host. */
+lbm_status lbm_mass(lbm_ctx* ctx, double* h_out);
+
+/* Number of interface-solid nodes of the installed geometry. */
+lbm_status lbm_interface_count(lbm_ctx* ctx, int64_t* n);
+
+/* Wait for the context's stream; returns LBM_ERR_CUDA on a pending fault. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* End-to-end run on host buffers: copies the mask and initial densities
+ * from host memory into the workspace, installs geometry and wetting,
+ * initialises, runs nsteps, and copies densities and velocity back (double
+ * [ny][nx] each; output pointers may be NULL). Uses the context's stream
+ * and workspace only (plus the staging area inside the workspace).
+ * Synchronises. */
+lbm_status lbm_run_host(lbm_ctx* ctx, const lbm_wetting_params* w, const uint8_t* h_mask,
+                        const double* h_rhoA, const double* h_rhoB, int32_t nsteps,
+                        double* h_rhoA_out, double* h_rhoB_out, double* h_ux_out,
+                        double* h_uy_out);
+
+/* Release the host context (not the caller's workspace). */
+lbm_status lbm_destroy(lbm_ctx* ctx);
+
+/* Static description of a status code. */
+const char* lbm_status_str(lbm_status s);
+
+/* Text of the last error recorded in ctx ("" if none). */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Number of kernels this context has launched since creation. */
+int64_t lbm_launch_count(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

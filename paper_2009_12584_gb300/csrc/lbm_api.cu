@@ -1,0 +1,557 @@
+// C ABI of the GB300 lattice-Boltzmann library (declared in include/lbm.h):
+// context, workspace carve-up, argument checks and kernel launches.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "lbm.h"
+#include "lbm_fused.cuh"
+#include "lbm_geometry.cuh"
+#include "lbm_kernels.cuh"
+
+using namespace lbm;
+
+struct lbm_ctx {
+  lbm_params prm;
+  Geo g;
+  Phys ph;
+  cudaStream_t stream;
+  int device;
+  int num_sms;
+  // workspace carve-up
+  char* ws;
+  size_t ws_bytes;
+  void* f[2];          // population buffers (storage type)
+  void* P;             // density plane pair (compute type)
+  uint16_t* flags;
+  int* iface_list;
+  int* scan_counts;    // per-block interface counts / offsets
+  int* small;          // [0] error count, [1] interface total
+  double* partial;     // mass partial sums
+  double* mass_out;    // 2 doubles
+  uint8_t* stage_mask; // lbm_run_host staging
+  double* stage;       // 4 arrays of nx*ny doubles
+  int64_t if_capacity;
+  int scan_blocks;
+  int mass_blocks;
+  int n_iface;
+  int cur;             // index of the buffer holding the current state
+  bool has_geometry, has_fields, has_wetting;
+  int64_t launches;
+  // lbm_step_profiled: when prof_on, every launch is bracketed by a pair of
+  // events from this pool and tagged with its kernel class
+  bool prof_on;
+  cudaEvent_t* prof_ev;
+  int* prof_cls;
+  int prof_n, prof_cap;
+  char err[512];
+};
+
+namespace {
+
+size_t elem_size(int storage) {
+  switch (storage) {
+    case LBM_STORE_FP32: return 4;
+    case LBM_STORE_FP64: return 8;
+    case LBM_STORE_FP16: return 2;
+    case LBM_STORE_BF16: return 2;
+  }
+  return 0;
+}
+size_t compute_size(int storage) { return storage == LBM_STORE_FP64 ? 8 : 4; }
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool make_geo(const lbm_params* p, Geo* g) {
+  if (p->nx < 4 || p->ny < 4) return false;
+  g->nx = p->nx;
+  g->ny = p->ny;
+  g->px = (int)align_up((size_t)p->nx + 2 * GH, 32);
+  g->py = p->ny + 2 * GH;
+  g->plane = (int64_t)g->px * g->py;
+  g->per_x = p->periodic_x ? 1 : 0;
+  g->per_y = p->periodic_y ? 1 : 0;
+  return g->plane < (int64_t(1) << 31) - 64;
+}
+
+struct Layout {
+  size_t f, P, flags, list, counts, small, partial, mass, smask, stage, total;
+};
+
+constexpr int MASS_BLOCKS = 1024;
+
+bool layout(const lbm_params* p, const Geo& g, Layout* L) {
+  const size_t A = 256;
+  const size_t es = elem_size(p->storage), cs = compute_size(p->storage);
+  if (!es) return false;
+  const int64_t N = (int64_t)p->nx * p->ny;
+  const int64_t cap = p->max_interface > 0 ? p->max_interface : N;
+  const int64_t scan_blocks = (N + SCAN_BLOCK - 1) / SCAN_BLOCK;
+  size_t off = 0;
+  L->f = off;        off = align_up(off + 2 * 18 * (size_t)g.plane * es, A);
+  L->P = off;        off = align_up(off + 2 * (size_t)g.plane * cs, A);
+  L->flags = off;    off = align_up(off + (size_t)g.plane * 2, A);
+  L->list = off;     off = align_up(off + (size_t)cap * 4, A);
+  L->counts = off;   off = align_up(off + (size_t)scan_blocks * 4, A);
+  L->small = off;    off = align_up(off + 64, A);
+  L->partial = off;  off = align_up(off + 2 * MASS_BLOCKS * 8, A);
+  L->mass = off;     off = align_up(off + 16, A);
+  L->smask = off;    off = align_up(off + (size_t)N, A);
+  L->stage = off;    off = align_up(off + 4 * (size_t)N * 8, A);
+  L->total = off;
+  return true;
+}
+
+lbm_status fail(lbm_ctx* c, lbm_status s, const char* msg) {
+  if (c) snprintf(c->err, sizeof(c->err), "%s", msg);
+  return s;
+}
+
+lbm_status check_cuda(lbm_ctx* c, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return LBM_OK;
+  if (c) snprintf(c->err, sizeof(c->err), "%s: %s", where, cudaGetErrorString(e));
+  return LBM_ERR_CUDA;
+}
+
+lbm_status after_launch(lbm_ctx* c, const char* where) {
+  c->launches++;
+  return check_cuda(c, cudaGetLastError(), where);
+}
+
+// Launch helper: runs fn() (which enqueues one kernel) and, while profiling,
+// records an event on each side of it.
+template <typename Fn>
+lbm_status launch(lbm_ctx* c, int cls, const char* where, Fn&& fn) {
+  const bool rec = c->prof_on && c->prof_n < c->prof_cap;
+  if (rec) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
+  fn();
+  lbm_status s = after_launch(c, where);
+  if (rec) {
+    cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
+    c->prof_cls[c->prof_n++] = cls;
+  }
+  return s;
+}
+
+dim3 node_grid(const Geo& g, int bx) { return dim3((g.nx + bx - 1) / bx, g.ny); }
+
+template <typename T>
+lbm_status launch_density_and_virtual(lbm_ctx* c, const T* f) {
+  using C = typename Pop<T>::C;
+  C* P = (C*)c->P;
+  lbm_status s = launch(c, LBM_KC_DENSITY, "k_density", [&] {
+    k_density<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>(f, P, c->flags, c->g, c->ph);
+  });
+  if (s) return s;
+  if (c->ph.bc == BC_VAVG && c->n_iface > 0) {
+    s = launch(c, LBM_KC_VIRTUAL, "k_virtual_density", [&] {
+      k_virtual_density<C><<<(c->n_iface + 127) / 128, 128, 0, c->stream>>>(P, c->flags, c->iface_list,
+                                                                             c->n_iface, c->g, c->ph);
+    });
+  }
+  return s;
+}
+
+template <typename T>
+lbm_status step_two_pass(lbm_ctx* c, int nsteps) {
+  for (int t = 0; t < nsteps; ++t) {
+    const T* fin = (const T*)c->f[c->cur];
+    T* fout = (T*)c->f[c->cur ^ 1];
+    lbm_status s = launch_density_and_virtual<T>(c, fin);
+    if (s) return s;
+    s = launch(c, LBM_KC_COLLIDE, "k_collide", [&] {
+      k_collide<T, 0><<<node_grid(c->g, 128), 128, 0, c->stream>>>(fin, fout, (const typename Pop<T>::C*)c->P,
+                                                                    c->flags, c->g, c->ph, nullptr);
+    });
+    if (s) return s;
+    c->cur ^= 1;
+  }
+  return LBM_OK;
+}
+
+template <typename T>
+lbm_status step_fused(lbm_ctx* c, int nsteps) {
+  for (int t = 0; t < nsteps; ++t) {
+    const T* fin = (const T*)c->f[c->cur];
+    T* fout = (T*)c->f[c->cur ^ 1];
+    lbm_status ls = LBM_OK;
+    lbm_status s = launch(c, LBM_KC_FUSED, "k_fused", [&] {
+      ls = launch_fused<T>(c->g, c->ph, fin, fout, c->flags, c->num_sms, c->stream);
+    });
+    if (ls) return fail(c, ls, "fused kernel launch rejected");
+    if (s) return s;
+    c->cur ^= 1;
+  }
+  return LBM_OK;
+}
+
+template <typename T>
+lbm_status do_step(lbm_ctx* c, int nsteps) {
+  const bool fused = c->prm.kernel != LBM_KERNEL_TWO_PASS && fused_supported<T>(c->g, c->ph);
+  return fused ? step_fused<T>(c, nsteps) : step_two_pass<T>(c, nsteps);
+}
+
+template <typename T, int MODE>
+lbm_status do_eval(lbm_ctx* c, double* out) {
+  const T* fin = (const T*)c->f[c->cur];
+  lbm_status s = launch_density_and_virtual<T>(c, fin);
+  if (s) return s;
+  k_collide<T, MODE><<<node_grid(c->g, 128), 128, 0, c->stream>>>(fin, nullptr, (const typename Pop<T>::C*)c->P,
+                                                                   c->flags, c->g, c->ph, out);
+  return after_launch(c, "k_collide(eval)");
+}
+
+template <typename T>
+lbm_status do_get_pops(lbm_ctx* c, double* out) {
+  k_get_populations<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>((const T*)c->f[c->cur], c->flags, c->g,
+                                                                     c->ph, out);
+  return after_launch(c, "k_get_populations");
+}
+
+template <typename T, int SRC>
+lbm_status do_set_state(lbm_ctx* c, const double* fin, const double* rA, const double* rB, const double* ux,
+                        const double* uy) {
+  k_set_state<T, SRC><<<node_grid(c->g, 128), 128, 0, c->stream>>>((T*)c->f[c->cur], c->flags, c->g, c->ph,
+                                                                     fin, rA, rB, ux, uy);
+  return after_launch(c, "k_set_state");
+}
+
+template <typename T>
+lbm_status do_mass(lbm_ctx* c) {
+  k_mass_partial<T><<<c->mass_blocks, 256, 0, c->stream>>>((const T*)c->f[c->cur], c->flags, c->g, c->ph,
+                                                           c->partial);
+  lbm_status s = after_launch(c, "k_mass_partial");
+  if (s) return s;
+  k_mass_final<<<1, 64, 0, c->stream>>>(c->partial, c->mass_blocks, c->mass_out);
+  return after_launch(c, "k_mass_final");
+}
+
+// Dispatch on the storage type.
+#define LBM_DISPATCH(c, CALL)                            \
+  switch ((c)->prm.storage) {                            \
+    case LBM_STORE_FP32: { using T = float; CALL; }      \
+    case LBM_STORE_FP64: { using T = double; CALL; }     \
+    case LBM_STORE_FP16: { using T = __half; CALL; }     \
+    default: { using T = __nv_bfloat16; CALL; }          \
+  }
+
+bool valid_params(const lbm_params* p) {
+  if (!p) return false;
+  if (p->nx < 4 || p->ny < 4) return false;
+  if (!(p->tau[0] > 0.5) || !(p->tau[1] > 0.5)) return false;
+  if (p->storage < LBM_STORE_FP32 || p->storage > LBM_STORE_BF16) return false;
+  if (p->kernel < LBM_KERNEL_AUTO || p->kernel > LBM_KERNEL_FUSED) return false;
+  if (p->max_interface < 0) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_status_str(lbm_status s) {
+  switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_STATE: return "call out of order";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_SPACE: return "workspace too small";
+    case LBM_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err : ""; }
+
+int64_t lbm_launch_count(const lbm_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+lbm_status lbm_workspace_bytes(const lbm_params* params, size_t* bytes) {
+  if (!valid_params(params) || !bytes) return LBM_ERR_ARG;
+  Geo g;
+  if (!make_geo(params, &g)) return LBM_ERR_ARG;
+  Layout L;
+  if (!layout(params, g, &L)) return LBM_ERR_ARG;
+  *bytes = L.total;
+  return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_params* params, void* d_workspace, size_t bytes, void* cuda_stream,
+                      lbm_ctx** out) {
+  if (!out) return LBM_ERR_ARG;
+  *out = nullptr;
+  if (!valid_params(params) || !d_workspace) return LBM_ERR_ARG;
+  if (((uintptr_t)d_workspace) % 256) return LBM_ERR_ARG;
+  Geo g;
+  Layout L;
+  if (!make_geo(params, &g) || !layout(params, g, &L)) return LBM_ERR_ARG;
+  if (bytes < L.total) return LBM_ERR_SPACE;
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_ERR_SPACE;
+  c->prm = *params;
+  if (!(c->prm.rho_ref[0] > 0)) c->prm.rho_ref[0] = 1.0;
+  if (!(c->prm.rho_ref[1] > 0)) c->prm.rho_ref[1] = 1.0;
+  c->g = g;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->ws = (char*)d_workspace;
+  c->ws_bytes = bytes;
+  const size_t es = elem_size(params->storage);
+  c->f[0] = c->ws + L.f;
+  c->f[1] = c->ws + L.f + 18 * (size_t)g.plane * es;
+  c->P = c->ws + L.P;
+  c->flags = (uint16_t*)(c->ws + L.flags);
+  c->iface_list = (int*)(c->ws + L.list);
+  c->scan_counts = (int*)(c->ws + L.counts);
+  c->small = (int*)(c->ws + L.small);
+  c->partial = (double*)(c->ws + L.partial);
+  c->mass_out = (double*)(c->ws + L.mass);
+  c->stage_mask = (uint8_t*)(c->ws + L.smask);
+  c->stage = (double*)(c->ws + L.stage);
+  const int64_t N = (int64_t)params->nx * params->ny;
+  c->if_capacity = params->max_interface > 0 ? params->max_interface : N;
+  c->scan_blocks = (int)((N + SCAN_BLOCK - 1) / SCAN_BLOCK);
+  c->mass_blocks = MASS_BLOCKS;
+  // physics defaults: Martys-Chen with no adhesion until lbm_set_wetting
+  Phys& ph = c->ph;
+  memset(&ph, 0, sizeof(ph));
+  for (int s = 0; s < 2; ++s) {
+    ph.omega[s] = 1.0 / params->tau[s];
+    ph.kF[s] = 1.0 - 0.5 / params->tau[s];
+    ph.chi[s] = 1.0;
+    ph.rho_ref[s] = params->storage >= LBM_STORE_FP16 ? c->prm.rho_ref[s] : 0.0;
+  }
+  ph.G_AB = params->G_AB;
+  ph.bc = BC_MC;
+  lbm_status s = check_cuda(c, cudaGetDevice(&c->device), "cudaGetDevice");
+  if (!s) s = check_cuda(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device),
+                         "cudaDeviceGetAttribute");
+  if (!s) s = check_cuda(c, cudaMemsetAsync(c->ws, 0, L.total, c->stream), "cudaMemsetAsync");
+  if (s) {
+    delete c;
+    return s;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_stream(lbm_ctx* c, void* cuda_stream) {
+  if (!c) return LBM_ERR_ARG;
+  c->stream = (cudaStream_t)cuda_stream;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* d_mask) {
+  if (!c || !d_mask) return LBM_ERR_ARG;
+  const Geo& g = c->g;
+  c->has_fields = false;
+  c->has_geometry = false;
+  lbm_status s = check_cuda(c, cudaMemsetAsync(c->small, 0, 64, c->stream), "cudaMemsetAsync");
+  if (s) return s;
+  k_flags<<<dim3((g.px + 127) / 128, g.py), 128, 0, c->stream>>>(d_mask, c->flags, g, c->small);
+  if ((s = after_launch(c, "k_flags"))) return s;
+  k_iface_count<<<c->scan_blocks, SCAN_BLOCK, 0, c->stream>>>(c->flags, g, c->scan_counts);
+  if ((s = after_launch(c, "k_iface_count"))) return s;
+  k_iface_scan<<<1, 1024, 0, c->stream>>>(c->scan_counts, c->scan_blocks, c->small + 1);
+  if ((s = after_launch(c, "k_iface_scan"))) return s;
+  k_iface_write<<<c->scan_blocks, SCAN_BLOCK, 0, c->stream>>>(c->flags, g, c->scan_counts,
+                                                              (int)c->if_capacity, c->iface_list);
+  if ((s = after_launch(c, "k_iface_write"))) return s;
+  // clear the density planes so solid cells read as zero
+  s = check_cuda(c, cudaMemsetAsync(c->P, 0, 2 * (size_t)g.plane * compute_size(c->prm.storage), c->stream),
+                 "cudaMemsetAsync");
+  if (s) return s;
+  int h[2];
+  s = check_cuda(c, cudaMemcpyAsync(h, c->small, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+  if (!s) s = check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (s) return s;
+  if (h[0] > 0) return fail(c, LBM_ERR_ARG, "fluid node on a non-periodic border");
+  if (h[1] > c->if_capacity) return fail(c, LBM_ERR_SPACE, "interface-solid list exceeds max_interface");
+  c->n_iface = h[1];
+  c->has_geometry = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_wetting(lbm_ctx* c, const lbm_wetting_params* w) {
+  if (!c || !w) return LBM_ERR_ARG;
+  if (w->kind < LBM_WET_MARTYS_CHEN || w->kind > LBM_WET_CONSTANT) return fail(c, LBM_ERR_ARG, "unknown wetting kind");
+  if (w->pairing != LBM_PAIR_CROSS && w->pairing != LBM_PAIR_SELF) return fail(c, LBM_ERR_ARG, "unknown pairing");
+  if (w->avg_stencil != 9 && w->avg_stencil != 25) return fail(c, LBM_ERR_ARG, "avg_stencil must be 9 or 25");
+  if (w->kind == LBM_WET_VIRTUAL_AVG)
+    for (int s = 0; s < 2; ++s)
+      if (!(w->chi[s] > 0.0 && w->chi[s] <= 2.0)) return fail(c, LBM_ERR_ARG, "chi outside (0, 2]");
+  c->ph.bc = w->kind;
+  c->ph.pairing = w->pairing;
+  c->ph.avg9 = w->avg_stencil == 9 ? 1 : 0;
+  for (int s = 0; s < 2; ++s) {
+    c->ph.G_s[s] = w->G_s[s];
+    c->ph.chi[s] = w->chi[s];
+    c->ph.rho_s[s] = w->rho_s[s];
+  }
+  c->has_wetting = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_init_fields(lbm_ctx* c, const double* rA, const double* rB, const double* ux, const double* uy) {
+  if (!c || !rA || !rB) return LBM_ERR_ARG;
+  if (!c->has_geometry) return fail(c, LBM_ERR_STATE, "lbm_init_fields before lbm_set_geometry");
+  c->cur = 0;
+  lbm_status s;
+  LBM_DISPATCH(c, s = (do_set_state<T, 1>(c, nullptr, rA, rB, ux, uy)); break);
+  if (!s) c->has_fields = true;
+  return s;
+}
+
+lbm_status lbm_set_populations(lbm_ctx* c, const double* fin) {
+  if (!c || !fin) return LBM_ERR_ARG;
+  if (!c->has_geometry) return fail(c, LBM_ERR_STATE, "lbm_set_populations before lbm_set_geometry");
+  c->cur = 0;
+  lbm_status s;
+  LBM_DISPATCH(c, s = (do_set_state<T, 0>(c, fin, nullptr, nullptr, nullptr, nullptr)); break);
+  if (!s) c->has_fields = true;
+  return s;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int32_t nsteps) {
+  if (!c || nsteps < 0) return LBM_ERR_ARG;
+  if (!c->has_geometry || !c->has_fields) return fail(c, LBM_ERR_STATE, "lbm_step before geometry and fields");
+  lbm_status s;
+  LBM_DISPATCH(c, s = do_step<T>(c, nsteps); break);
+  return s;
+}
+
+lbm_status lbm_step_profiled(lbm_ctx* c, int32_t nsteps, double* h_ms, int64_t* h_launches) {
+  if (!c || nsteps < 0) return LBM_ERR_ARG;
+  if (!c->has_geometry || !c->has_fields) return fail(c, LBM_ERR_STATE, "lbm_step before geometry and fields");
+  const int cap = 3 * nsteps + 4;
+  c->prof_ev = (cudaEvent_t*)calloc((size_t)2 * cap, sizeof(cudaEvent_t));
+  c->prof_cls = (int*)calloc((size_t)cap, sizeof(int));
+  if (!c->prof_ev || !c->prof_cls) {
+    free(c->prof_ev);
+    free(c->prof_cls);
+    c->prof_ev = nullptr;
+    c->prof_cls = nullptr;
+    return fail(c, LBM_ERR_SPACE, "host allocation for profiling events failed");
+  }
+  lbm_status s = LBM_OK;
+  int created = 0;
+  for (; created < 2 * cap && !s; ++created)
+    s = check_cuda(c, cudaEventCreate(&c->prof_ev[created]), "cudaEventCreate");
+  if (!s) {
+    c->prof_on = true;
+    c->prof_n = 0;
+    c->prof_cap = cap;
+    LBM_DISPATCH(c, s = do_step<T>(c, nsteps); break);
+    c->prof_on = false;
+  }
+  if (!s) s = check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  double ms[LBM_KC_COUNT] = {0, 0, 0, 0};
+  int64_t cnt[LBM_KC_COUNT] = {0, 0, 0, 0};
+  if (!s)
+    for (int i = 0; i < c->prof_n && !s; ++i) {
+      float t = 0.f;
+      s = check_cuda(c, cudaEventElapsedTime(&t, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]),
+                     "cudaEventElapsedTime");
+      ms[c->prof_cls[i]] += t;
+      cnt[c->prof_cls[i]] += 1;
+    }
+  for (int i = 0; i < created; ++i) cudaEventDestroy(c->prof_ev[i]);
+  free(c->prof_ev);
+  free(c->prof_cls);
+  c->prof_ev = nullptr;
+  c->prof_cls = nullptr;
+  c->prof_n = c->prof_cap = 0;
+  if (s) return s;
+  for (int k = 0; k < LBM_KC_COUNT; ++k) {
+    if (h_ms) h_ms[k] = ms[k];
+    if (h_launches) h_launches[k] = cnt[k];
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx* c, double* rA, double* rB, double* ux, double* uy) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->has_geometry || !c->has_fields) return fail(c, LBM_ERR_STATE, "lbm_moments before geometry and fields");
+  const int64_t N = (int64_t)c->g.nx * c->g.ny;
+  double* tmp = c->stage;  // 4 * N doubles
+  lbm_status s;
+  LBM_DISPATCH(c, s = (do_eval<T, 1>(c, tmp)); break);
+  if (s) return s;
+  double* outs[4] = {rA, rB, ux, uy};
+  for (int a = 0; a < 4 && !s; ++a)
+    if (outs[a])
+      s = check_cuda(c, cudaMemcpyAsync(outs[a], tmp + a * N, N * 8, cudaMemcpyDeviceToDevice, c->stream),
+                     "cudaMemcpyAsync");
+  return s;
+}
+
+lbm_status lbm_forces(lbm_ctx* c, double* F) {
+  if (!c || !F) return LBM_ERR_ARG;
+  if (!c->has_geometry || !c->has_fields) return fail(c, LBM_ERR_STATE, "lbm_forces before geometry and fields");
+  lbm_status s;
+  LBM_DISPATCH(c, s = (do_eval<T, 2>(c, F)); break);
+  return s;
+}
+
+lbm_status lbm_get_populations(lbm_ctx* c, double* out) {
+  if (!c || !out) return LBM_ERR_ARG;
+  if (!c->has_geometry || !c->has_fields) return fail(c, LBM_ERR_STATE, "lbm_get_populations before fields");
+  lbm_status s;
+  LBM_DISPATCH(c, s = do_get_pops<T>(c, out); break);
+  return s;
+}
+
+lbm_status lbm_mass(lbm_ctx* c, double* h_out) {
+  if (!c || !h_out) return LBM_ERR_ARG;
+  if (!c->has_geometry || !c->has_fields) return fail(c, LBM_ERR_STATE, "lbm_mass before geometry and fields");
+  lbm_status s;
+  LBM_DISPATCH(c, s = do_mass<T>(c); break);
+  if (s) return s;
+  s = check_cuda(c, cudaMemcpyAsync(h_out, c->mass_out, 16, cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+  if (!s) s = check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  return s;
+}
+
+lbm_status lbm_interface_count(lbm_ctx* c, int64_t* n) {
+  if (!c || !n) return LBM_ERR_ARG;
+  if (!c->has_geometry) return fail(c, LBM_ERR_STATE, "no geometry");
+  *n = c->n_iface;
+  return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx* c) {
+  if (!c) return LBM_ERR_ARG;
+  return check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+}
+
+lbm_status lbm_run_host(lbm_ctx* c, const lbm_wetting_params* w, const uint8_t* h_mask, const double* h_rhoA,
+                        const double* h_rhoB, int32_t nsteps, double* oA, double* oB, double* oux, double* ouy) {
+  if (!c || !w || !h_mask || !h_rhoA || !h_rhoB || nsteps < 0) return LBM_ERR_ARG;
+  const int64_t N = (int64_t)c->g.nx * c->g.ny;
+  double* in = c->stage;  // rhoA at [0, N), rhoB at [N, 2N)
+  lbm_status s = check_cuda(c, cudaMemcpyAsync(c->stage_mask, h_mask, N, cudaMemcpyHostToDevice, c->stream),
+                            "cudaMemcpyAsync");
+  if (!s) s = check_cuda(c, cudaMemcpyAsync(in, h_rhoA, N * 8, cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync");
+  if (!s) s = check_cuda(c, cudaMemcpyAsync(in + N, h_rhoB, N * 8, cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync");
+  if (!s) s = lbm_set_geometry(c, c->stage_mask);
+  if (!s) s = lbm_set_wetting(c, w);
+  if (!s) s = lbm_init_fields(c, in, in + N, nullptr, nullptr);
+  if (!s) s = lbm_step(c, nsteps);
+  if (s) return s;
+  LBM_DISPATCH(c, s = (do_eval<T, 1>(c, c->stage)); break);
+  double* outs[4] = {oA, oB, oux, ouy};
+  for (int a = 0; a < 4 && !s; ++a)
+    if (outs[a])
+      s = check_cuda(c, cudaMemcpyAsync(outs[a], c->stage + a * N, N * 8, cudaMemcpyDeviceToHost, c->stream),
+                     "cudaMemcpyAsync");
+  if (!s) s = check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  return s;
+}
+
+lbm_status lbm_destroy(lbm_ctx* c) {
+  if (!c) return LBM_ERR_ARG;
+  delete c;
+  return LBM_OK;
+}
+
+}  // extern "C"

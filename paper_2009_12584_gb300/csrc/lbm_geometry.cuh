@@ -1,0 +1,135 @@
+// Geometry set-up kernels: per-node flags from the caller's mask (with
+// periodic wrap or solid ghosts) and the deterministic compaction of the
+// interface-solid list (solid nodes with a fluid D2Q9 neighbour, identified
+// once per geometry, Sec. 3.2 of arXiv:2009.12584).
+#pragma once
+
+#include "lbm_common.cuh"
+
+namespace lbm {
+
+// Solidity of logical node (x, y), which may lie outside the owned range.
+__device__ __forceinline__ bool solid_at(const uint8_t* __restrict__ mask, const Geo& g, int x, int y) {
+  if (x < 0 || x >= g.nx) {
+    if (!g.per_x) return true;
+    x = (x % g.nx + g.nx) % g.nx;
+  }
+  if (y < 0 || y >= g.ny) {
+    if (!g.per_y) return true;
+    y = (y % g.ny + g.ny) % g.ny;
+  }
+  return mask[(int64_t)y * g.nx + x] != 0;
+}
+
+// One thread per padded cell. err[0] counts fluid nodes on a walled border.
+__global__ void k_flags(const uint8_t* __restrict__ mask, uint16_t* __restrict__ flags, Geo g,
+                        int* __restrict__ err) {
+  const int px = blockIdx.x * blockDim.x + threadIdx.x, py = blockIdx.y;
+  if (px >= g.px) return;
+  const int x = px - GH, y = py - GH;
+  const bool owned = x >= 0 && x < g.nx && y >= 0 && y < g.ny;
+  // padding columns beyond nx + GH are outside every stencil; mark solid
+  const bool in_halo = x >= -GH && x < g.nx + GH;
+  uint16_t fl = 0;
+  if (!in_halo || solid_at(mask, g, x, y)) fl |= F_SOLID;
+  if (owned) {
+    bool any_fluid_nb = false;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+      if (solid_at(mask, g, x + cx_of(i), y + cy_of(i))) {
+        fl |= nb_bit(i);
+      } else {
+        any_fluid_nb = true;
+      }
+    }
+    if ((fl & F_SOLID) && any_fluid_nb) fl |= F_IFACE;
+    if (!(fl & F_SOLID)) {
+      const bool on_wall = (!g.per_x && (x == 0 || x == g.nx - 1)) || (!g.per_y && (y == 0 || y == g.ny - 1));
+      if (on_wall) atomicAdd(err, 1);
+    }
+  }
+  flags[(int64_t)py * g.px + px] = fl;
+}
+
+constexpr int SCAN_BLOCK = 256;
+
+// Pass 1: interface-solid nodes per block of SCAN_BLOCK owned nodes.
+__global__ void __launch_bounds__(SCAN_BLOCK) k_iface_count(const uint16_t* __restrict__ flags, Geo g,
+                                                            int* __restrict__ counts) {
+  const int64_t n = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+  const int64_t N = (int64_t)g.nx * g.ny;
+  bool hit = false;
+  if (n < N) hit = flags[g.idx((int)(n % g.nx), (int)(n / g.nx))] & F_IFACE;
+  const int c = __syncthreads_count(hit);
+  if (threadIdx.x == 0) counts[blockIdx.x] = c;
+}
+
+// Pass 2: exclusive scan of the per-block counts in one block (fixed order).
+__global__ void __launch_bounds__(1024) k_iface_scan(int* __restrict__ counts, int nblocks,
+                                                     int* __restrict__ total) {
+  __shared__ int carry;
+  __shared__ int warp_sums[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nblocks; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int v = i < nblocks ? counts[i] : 0;
+    int x = v;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int s = warp_sums[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += t;
+      }
+      warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const int incl = x + (wid ? warp_sums[wid - 1] : 0);
+    if (i < nblocks) counts[i] = carry + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+// Pass 3: write padded indices of interface-solid nodes in node order.
+__global__ void __launch_bounds__(SCAN_BLOCK) k_iface_write(const uint16_t* __restrict__ flags, Geo g,
+                                                            const int* __restrict__ offsets, int capacity,
+                                                            int* __restrict__ list) {
+  __shared__ int warp_base[SCAN_BLOCK / 32];
+  const int64_t n = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+  const int64_t N = (int64_t)g.nx * g.ny;
+  int k = 0;
+  bool hit = false;
+  if (n < N) {
+    k = g.idx((int)(n % g.nx), (int)(n / g.nx));
+    hit = flags[k] & F_IFACE;
+  }
+  const unsigned ball = __ballot_sync(0xffffffffu, hit);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) warp_base[wid] = __popc(ball);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int w = 0; w < SCAN_BLOCK / 32; ++w) {
+      const int c = warp_base[w];
+      warp_base[w] = acc;
+      acc += c;
+    }
+  }
+  __syncthreads();
+  if (hit) {
+    const int pos = offsets[blockIdx.x] + warp_base[wid] + __popc(ball & ((1u << lane) - 1u));
+    if (pos < capacity) list[pos] = k;
+  }
+}
+
+}  // namespace lbm

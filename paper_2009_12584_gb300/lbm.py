@@ -1,0 +1,278 @@
+"""Thin ctypes binding of the C ABI in ``include/lbm.h``.
+
+Argument marshalling only: PyTorch provides the device memory (the workspace
+and the caller's arrays) and the CUDA stream; every step of the computation
+runs in the CUDA library ``liblbm_gb300.so``. There is no CPU fallback: if
+the library has not been built, or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm_gb300.so")
+
+OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_SPACE, ERR_TIMEOUT = range(6)
+WET_MARTYS_CHEN, WET_LLKC, WET_VIRTUAL_AVG, WET_CONSTANT = range(4)
+PAIR_CROSS, PAIR_SELF = 0, 1
+STORAGE = {"fp32": 0, "fp64": 1, "fp16": 2, "bf16": 3}
+KERNEL = {"auto": 0, "two_pass": 1, "fused": 2}
+WETTING = {"martys_chen": 0, "mc": 0, "llkc": 1, "virtual_avg": 2, "improved": 2, "constant": 3}
+
+
+class LbmParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
+        ("tau", ctypes.c_double * 2), ("G_AB", ctypes.c_double),
+        ("storage", ctypes.c_int32), ("kernel", ctypes.c_int32),
+        ("rho_ref", ctypes.c_double * 2), ("max_interface", ctypes.c_int64),
+    ]
+
+
+class LbmWetting(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("pairing", ctypes.c_int32),
+        ("avg_stencil", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("G_s", ctypes.c_double * 2), ("chi", ctypes.c_double * 2),
+        ("rho_s", ctypes.c_double * 2),
+    ]
+
+
+EXPORTS = [
+    "lbm_workspace_bytes", "lbm_create", "lbm_set_stream", "lbm_set_geometry", "lbm_set_wetting",
+    "lbm_init_fields", "lbm_step", "lbm_step_profiled", "lbm_moments", "lbm_forces", "lbm_get_populations",
+    "lbm_set_populations", "lbm_mass", "lbm_interface_count", "lbm_sync", "lbm_run_host",
+    "lbm_destroy", "lbm_status_str", "lbm_last_error", "lbm_launch_count",
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({_status_str(status)}) {detail}".strip())
+
+
+def _status_str(s):
+    try:
+        return load().lbm_status_str(s).decode()
+    except Exception:  # pragma: no cover - only while reporting another error
+        return "?"
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Open the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with `python -m paper_2009_12584_gb300.build` "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+        P = ctypes.POINTER(LbmParams)
+        W = ctypes.POINTER(LbmWetting)
+        sig = {
+            "lbm_workspace_bytes": [P, ctypes.POINTER(ctypes.c_size_t)],
+            "lbm_create": [P, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
+            "lbm_set_stream": [vp, vp],
+            "lbm_set_geometry": [vp, vp],
+            "lbm_set_wetting": [vp, W],
+            "lbm_init_fields": [vp, dp, dp, dp, dp],
+            "lbm_step": [vp, i32],
+            "lbm_step_profiled": [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)],
+            "lbm_moments": [vp, dp, dp, dp, dp],
+            "lbm_forces": [vp, dp],
+            "lbm_get_populations": [vp, dp],
+            "lbm_set_populations": [vp, dp],
+            "lbm_mass": [vp, ctypes.POINTER(ctypes.c_double)],
+            "lbm_interface_count": [vp, ctypes.POINTER(i64)],
+            "lbm_sync": [vp],
+            "lbm_run_host": [vp, W, vp, vp, vp, i32, vp, vp, vp, vp],
+            "lbm_destroy": [vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        lib.lbm_status_str.argtypes = [ctypes.c_int]
+        lib.lbm_status_str.restype = ctypes.c_char_p
+        lib.lbm_last_error.argtypes = [vp]
+        lib.lbm_last_error.restype = ctypes.c_char_p
+        lib.lbm_launch_count.argtypes = [vp]
+        lib.lbm_launch_count.restype = ctypes.c_int64
+        _lib = lib
+        return lib
+
+
+def make_params(nx, ny, *, tau=(1.0, 1.0), G_AB=3.0, periodic_x=False, periodic_y=False,
+                storage="fp32", kernel="auto", rho_ref=(1.0, 1.0), max_interface=0) -> LbmParams:
+    p = LbmParams()
+    p.nx, p.ny = int(nx), int(ny)
+    p.periodic_x, p.periodic_y = int(bool(periodic_x)), int(bool(periodic_y))
+    p.tau[0], p.tau[1] = tau
+    p.G_AB = G_AB
+    p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    p.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
+    p.rho_ref[0], p.rho_ref[1] = rho_ref
+    p.max_interface = int(max_interface)
+    return p
+
+
+def make_wetting(kind="martys_chen", *, G_s=(0.0, 0.0), chi=(1.0, 1.0), rho_s=(0.0, 0.0),
+                 pairing=PAIR_CROSS, avg_stencil=25) -> LbmWetting:
+    w = LbmWetting()
+    w.kind = WETTING[kind] if isinstance(kind, str) else int(kind)
+    w.pairing = int(pairing)
+    w.avg_stencil = int(avg_stencil)
+    w.G_s[0], w.G_s[1] = G_s
+    w.chi[0], w.chi[1] = chi
+    w.rho_s[0], w.rho_s[1] = rho_s
+    return w
+
+
+def workspace_bytes(params: LbmParams) -> int:
+    n = ctypes.c_size_t()
+    st = load().lbm_workspace_bytes(ctypes.byref(params), ctypes.byref(n))
+    if st:
+        raise LbmError(st, "lbm_workspace_bytes")
+    return n.value
+
+
+class Simulation:
+    """One simulation context on the current CUDA device and stream."""
+
+    def __init__(self, nx, ny, *, stream=None, **kw):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2009_12584_gb300 needs a CUDA GPU (there is no CPU fallback)")
+        self.torch = torch
+        self.lib = load()
+        self.nx, self.ny = int(nx), int(ny)
+        self.params = make_params(nx, ny, **kw)
+        self.storage = kw.get("storage", "fp32")
+        nbytes = workspace_bytes(self.params)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        self._check(self.lib.lbm_create(ctypes.byref(self.params), self.workspace.data_ptr(), nbytes,
+                                        self.stream.cuda_stream, ctypes.byref(h)), "lbm_create", ctx=False)
+        self.h = h
+        self.mask = None
+
+    # -- helpers -----------------------------------------------------------------
+    def _check(self, st, where, ctx=True):
+        if st != OK:
+            detail = ""
+            if ctx and getattr(self, "h", None):
+                detail = self.lib.lbm_last_error(self.h).decode()
+            raise LbmError(st, where, detail)
+
+    def _dev(self, a, dtype):
+        t = self.torch
+        if isinstance(a, np.ndarray):
+            a = t.from_numpy(np.ascontiguousarray(a))
+        return a.to(device="cuda", dtype=dtype).contiguous()
+
+    # -- API -----------------------------------------------------------------------
+    def set_geometry(self, mask):
+        self.mask = self._dev(mask, self.torch.uint8).reshape(self.ny, self.nx)
+        self._check(self.lib.lbm_set_geometry(self.h, self.mask.data_ptr()), "lbm_set_geometry")
+        return self
+
+    def set_wetting(self, kind="martys_chen", **kw):
+        self.wetting = make_wetting(kind, **kw)
+        self._check(self.lib.lbm_set_wetting(self.h, ctypes.byref(self.wetting)), "lbm_set_wetting")
+        return self
+
+    def init_fields(self, rhoA, rhoB, ux=None, uy=None):
+        f64 = self.torch.float64
+        self._init = [self._dev(a, f64) if a is not None else None for a in (rhoA, rhoB, ux, uy)]
+        ptr = [a.data_ptr() if a is not None else None for a in self._init]
+        self._check(self.lib.lbm_init_fields(self.h, *ptr), "lbm_init_fields")
+        return self
+
+    def step(self, n=1):
+        self._check(self.lib.lbm_step(self.h, int(n)), "lbm_step")
+        return self
+
+    def step_profiled(self, n):
+        """Advance n steps timing every kernel; returns (ms, launches) dicts
+        keyed by kernel class (density, virtual, collide, fused)."""
+        ms = (ctypes.c_double * 4)()
+        cnt = (ctypes.c_int64 * 4)()
+        self._check(self.lib.lbm_step_profiled(self.h, int(n), ms, cnt), "lbm_step_profiled")
+        names = ("density", "virtual", "collide", "fused")
+        return dict(zip(names, list(ms))), dict(zip(names, list(cnt)))
+
+    def moments(self):
+        t = self.torch
+        out = t.empty((4, self.ny, self.nx), dtype=t.float64, device="cuda")
+        ptrs = [out[i].data_ptr() for i in range(4)]
+        self._check(self.lib.lbm_moments(self.h, *ptrs), "lbm_moments")
+        return out[0], out[1], out[2:4]
+
+    def forces(self):
+        t = self.torch
+        out = t.empty((2, 2, self.ny, self.nx), dtype=t.float64, device="cuda")
+        self._check(self.lib.lbm_forces(self.h, out.data_ptr()), "lbm_forces")
+        return out
+
+    def populations(self):
+        t = self.torch
+        out = t.empty((2, 9, self.ny, self.nx), dtype=t.float64, device="cuda")
+        self._check(self.lib.lbm_get_populations(self.h, out.data_ptr()), "lbm_get_populations")
+        return out
+
+    def set_populations(self, f):
+        self._setf = self._dev(f, self.torch.float64).reshape(2, 9, self.ny, self.nx)
+        self._check(self.lib.lbm_set_populations(self.h, self._setf.data_ptr()), "lbm_set_populations")
+        return self
+
+    def mass(self):
+        out = (ctypes.c_double * 2)()
+        self._check(self.lib.lbm_mass(self.h, out), "lbm_mass")
+        return np.array([out[0], out[1]])
+
+    def interface_count(self):
+        n = ctypes.c_int64()
+        self._check(self.lib.lbm_interface_count(self.h, ctypes.byref(n)), "lbm_interface_count")
+        return n.value
+
+    def sync(self):
+        self._check(self.lib.lbm_sync(self.h), "lbm_sync")
+
+    @property
+    def launch_count(self):
+        return self.lib.lbm_launch_count(self.h)
+
+    def run_host(self, wetting: LbmWetting, mask, rhoA, rhoB, nsteps, outputs=None):
+        """End-to-end call on host arrays (pinned torch CPU tensors or numpy)."""
+        def hp(a):
+            if a is None:
+                return None
+            if isinstance(a, np.ndarray):
+                return a.ctypes.data
+            return a.data_ptr()
+        outs = outputs if outputs is not None else [None] * 4
+        self._check(self.lib.lbm_run_host(self.h, ctypes.byref(wetting), hp(mask), hp(rhoA), hp(rhoB),
+                                          int(nsteps), *[hp(o) for o in outs]), "lbm_run_host")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,84 @@
+"""The C-ABI library loads without a GPU, exports every function that
+include/lbm.h declares, and the ctypes mirrors of its structs have the
+C layout (checked against a C program compiled from the header)."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2009_12584_gb300 import build, lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return ctypes.CDLL(build.LIB_PATH)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(lbm.EXPORTS) <= set(names)
+
+
+def test_status_strings_without_gpu(lib):
+    lib.lbm_status_str.restype = ctypes.c_char_p
+    assert lib.lbm_status_str(0) == b"ok"
+    assert lib.lbm_status_str(2) == b"call out of order"
+
+
+def test_workspace_bytes_and_argument_checks_without_gpu():
+    lbm.load()
+    p = lbm.make_params(8192, 8192, periodic_x=True, periodic_y=True)
+    n = lbm.workspace_bytes(p)
+    # two population buffers of 18 FP32 planes dominate
+    assert n > 2 * 18 * 8192 * 8192 * 4
+    with pytest.raises(lbm.LbmError):
+        lbm.workspace_bytes(lbm.make_params(3, 8))
+    with pytest.raises(lbm.LbmError):
+        lbm.workspace_bytes(lbm.make_params(8, 8, tau=(0.5, 1.0)))
+    with pytest.raises(lbm.LbmError):
+        lbm.workspace_bytes(lbm.make_params(8, 8, storage=7))
+    n64 = lbm.workspace_bytes(lbm.make_params(64, 64, storage="fp64"))
+    n16 = lbm.workspace_bytes(lbm.make_params(64, 64, storage="fp16"))
+    assert n64 > n16
+
+
+def test_struct_layout_matches_header():
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "lbm.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(lbm_params), offsetof(lbm_params, tau),
+         offsetof(lbm_params, storage), offsetof(lbm_params, rho_ref), offsetof(lbm_params, max_interface));
+  printf("%zu %zu %zu %zu\n", sizeof(lbm_wetting_params), offsetof(lbm_wetting_params, G_s),
+         offsetof(lbm_wetting_params, chi), offsetof(lbm_wetting_params, rho_s));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "layout.c")
+        exe = os.path.join(d, "layout")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        out = subprocess.check_output([exe], text=True).split("\n")
+    a = [int(v) for v in out[0].split()]
+    b = [int(v) for v in out[1].split()]
+    P, W = lbm.LbmParams, lbm.LbmWetting
+    assert a == [ctypes.sizeof(P), P.tau.offset, P.storage.offset, P.rho_ref.offset, P.max_interface.offset]
+    assert b == [ctypes.sizeof(W), W.G_s.offset, W.chi.offset, W.rho_s.offset]

@@ -1,0 +1,252 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Element-by-element comparisons on seeded inputs at sizes the oracle runs in
+seconds (several 128-node tiles plus a ragged tail), every wetting scheme,
+both kernel schedules, every storage format, and the edge cases of the
+method. Tolerances: FP64 storage 1e-11 (rounding order only); FP32 storage
+max|drho|/rho <= 1e-5 and max|du| <= 1e-7 after 1000 steps.
+"""
+import hashlib
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_12584_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from paper_2009_12584_gb300 import lbm  # noqa: E402
+
+KERNELS = ["two_pass", "fused"]
+
+WETTINGS = {
+    "mc": (dict(bc=oracle.BC_MARTYS_CHEN, G_s=(-0.2, 0.2)), ("martys_chen", dict(G_s=(-0.2, 0.2)))),
+    "llkc": (dict(bc=oracle.BC_LLKC, G_s=(-0.5, 0.5)), ("llkc", dict(G_s=(-0.5, 0.5)))),
+    "llkc_self": (dict(bc=oracle.BC_LLKC, G_s=(-0.5, 0.3), pairing=oracle.PAIR_SELF),
+                  ("llkc", dict(G_s=(-0.5, 0.3), pairing=lbm.PAIR_SELF))),
+    "improved": (dict(bc=oracle.BC_VIRTUAL_AVG, G_s=(3.0, 3.0), chi=(1.2, 0.8)),
+                 ("virtual_avg", dict(G_s=(3.0, 3.0), chi=(1.2, 0.8)))),
+    "improved_self_d2q9": (dict(bc=oracle.BC_VIRTUAL_AVG, G_s=(2.5, 3.5), chi=(0.9, 1.3),
+                                pairing=oracle.PAIR_SELF, avg_stencil=9),
+                           ("virtual_avg", dict(G_s=(2.5, 3.5), chi=(0.9, 1.3), pairing=lbm.PAIR_SELF,
+                                                avg_stencil=9))),
+    "constant": (dict(bc=oracle.BC_CONSTANT, G_s=(3.0, 3.0), rho_s=(0.3, 0.7)),
+                 ("constant", dict(G_s=(3.0, 3.0), rho_s=(0.3, 0.7)))),
+}
+
+
+_ORACLE_CACHE = {}
+
+
+def _oracle_run(nx, ny, mask, rA, rB, steps, wet, periodic, tau, ux, uy):
+    """Oracle state after ``steps``; cached so that both kernel schedules are
+    compared with one oracle run."""
+    h = hashlib.sha1()
+    for a in (mask, rA, rB, ux, uy):
+        h.update(b"none" if a is None else np.ascontiguousarray(a).tobytes())
+    key = (nx, ny, steps, wet, periodic, tau, h.hexdigest())
+    if key not in _ORACLE_CACHE:
+        okw, _ = WETTINGS[wet]
+        o = oracle.Oracle(nx, ny, mask, tau=tau, periodic_x=periodic[0], periodic_y=periodic[1], **okw)
+        o.init(rA, rB, ux, uy).step(steps)
+        _ORACLE_CACHE[key] = o
+    return _ORACLE_CACHE[key]
+
+
+def run_pair(nx, ny, mask, rA, rB, steps, wet, *, periodic=(False, False), storage="fp64",
+             kernel="two_pass", tau=(1.0, 1.0), ux=None, uy=None):
+    _, (kind, gkw) = WETTINGS[wet]
+    o = _oracle_run(nx, ny, mask, rA, rB, steps, wet, tuple(periodic), tuple(tau), ux, uy)
+    sim = lbm.Simulation(nx, ny, tau=tau, periodic_x=periodic[0], periodic_y=periodic[1],
+                         storage=storage, kernel=kernel)
+    sim.set_geometry(mask).set_wetting(kind, **gkw).init_fields(rA, rB, ux, uy).step(steps)
+    rhoA, rhoB, u = sim.moments()
+    torch.cuda.synchronize()
+    return o, sim, (rhoA.cpu().numpy(), rhoB.cpu().numpy(), u.cpu().numpy())
+
+
+def errors(o, gpu, mask):
+    rho, rt, F, u = o.fields()
+    fl = mask == 0
+    d_rho = max((np.abs(gpu[0] - rho[0]) / rho[0])[fl].max(), (np.abs(gpu[1] - rho[1]) / rho[1])[fl].max())
+    d_u = np.abs(gpu[2] - u)[:, fl].max()
+    return d_rho, d_u
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("wet", list(WETTINGS))
+def test_fp64_inclined_wall(wet, kernel):
+    """FP64 storage: agreement to rounding on an off-grid wall (two 128-node
+    tiles plus a ragged tail), every wetting scheme."""
+    nx, ny = 150, 70
+    mask = inputs.inclined_wall_mask(nx, ny, 20.0, 12)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, ny / 2, 12)
+    o, sim, g = run_pair(nx, ny, mask, rA, rB, 200, wet, kernel=kernel)
+    d_rho, d_u = errors(o, g, mask)
+    assert d_rho < 1e-11 and d_u < 1e-12, (d_rho, d_u)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("wet", ["mc", "llkc", "improved"])
+def test_fp64_periodic_salt(wet, kernel):
+    """Fully periodic box with isolated solid nodes, one-node gaps and
+    corners; random densities and velocities exercise every term."""
+    nx, ny = 37, 29
+    mask = inputs.random_solid_mask(nx, ny, seed=11, fraction=0.15)
+    rA, rB, ux, uy = inputs.random_fields(nx, ny, seed=12, lo=0.2, hi=0.8, umax=0.02)
+    o, sim, g = run_pair(nx, ny, mask, rA, rB, 60, wet, periodic=(True, True), kernel=kernel,
+                         tau=(0.8, 1.3), ux=ux, uy=uy)
+    d_rho, d_u = errors(o, g, mask)
+    assert d_rho < 1e-11 and d_u < 1e-12, (d_rho, d_u)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("wet", ["mc", "llkc", "improved"])
+def test_fp32_inclined_wall_1000_steps(wet, kernel):
+    """FP32 storage and arithmetic after 1000 steps: max|drho|/rho <= 1e-5,
+    max|du| <= 1e-7 against FP64."""
+    nx, ny = 200, 100
+    mask = inputs.inclined_wall_mask(nx, ny, 20.0, 15)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, ny / 2, 15)
+    o, sim, g = run_pair(nx, ny, mask, rA, rB, 1000, wet, storage="fp32", kernel=kernel)
+    d_rho, d_u = errors(o, g, mask)
+    assert d_rho <= 1e-5 and d_u <= 1e-7, (d_rho, d_u)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp32_flat_wall_droplet_at_rest(kernel):
+    """100x50 channel periodic in x, flat wall along y = 0, semicircular
+    droplet (1.0 in, 0.03 out), Martys-Chen at neutral wetting: parity after
+    1000 steps and no sliding."""
+    nx, ny = 100, 50
+    mask = inputs.flat_wall_mask(nx, ny)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, 0.5, 15, 1.0, 0.03)
+    okw = dict(bc=oracle.BC_MARTYS_CHEN, G_s=(0.0, 0.0))
+    o = oracle.Oracle(nx, ny, mask, periodic_x=True, **okw).init(rA, rB).step(1000)
+    sim = lbm.Simulation(nx, ny, periodic_x=True, storage="fp32", kernel=kernel)
+    sim.set_geometry(mask).set_wetting("martys_chen", G_s=(0.0, 0.0)).init_fields(rA, rB).step(1000)
+    rhoA, rhoB, u = sim.moments()
+    g = (rhoA.cpu().numpy(), rhoB.cpu().numpy(), u.cpu().numpy())
+    d_rho, d_u = errors(o, g, mask)
+    assert d_rho <= 1e-5 and d_u <= 1e-7, (d_rho, d_u)
+    w = np.maximum(g[0] - 0.03, 0)
+    assert abs((w * g[2][0]).sum() / w.sum()) < 1e-7
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("nx,ny,per", [(4, 4, (True, True)), (5, 4, (True, False)), (131, 9, (True, True)),
+                                       (129, 6, (False, True)), (8, 130, (True, False))])
+def test_fp64_edge_sizes(nx, ny, per, kernel):
+    """Smallest grids, odd and ragged sizes, periodic axes shorter than two
+    ghost layers."""
+    mask = inputs.random_solid_mask(nx, ny, seed=nx * 1000 + ny, fraction=0.1, periodic_x=per[0],
+                                    periodic_y=per[1])
+    rA, rB, ux, uy = inputs.random_fields(nx, ny, seed=3, lo=0.2, hi=0.9, umax=0.01)
+    o, sim, g = run_pair(nx, ny, mask, rA, rB, 25, "improved", periodic=per, kernel=kernel, ux=ux, uy=uy)
+    d_rho, d_u = errors(o, g, mask)
+    assert d_rho < 1e-11 and d_u < 1e-12, (d_rho, d_u)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp64_no_solid_and_isolated_fluid(kernel):
+    """A box with no solid node, and one whose only fluid node has eight
+    solid neighbours (everything bounces back)."""
+    nx, ny = 16, 12
+    rA, rB, ux, uy = inputs.random_fields(nx, ny, seed=4, lo=0.2, hi=0.9, umax=0.02)
+    mask = np.zeros((ny, nx), np.uint8)
+    o, sim, g = run_pair(nx, ny, mask, rA, rB, 30, "mc", periodic=(True, True), kernel=kernel, ux=ux, uy=uy)
+    assert max(errors(o, g, mask)) < 1e-11
+    mask = np.ones((ny, nx), np.uint8)
+    mask[5, 7] = 0
+    o, sim, g = run_pair(nx, ny, mask, rA, rB, 30, "improved", kernel=kernel, ux=ux, uy=uy)
+    assert max(errors(o, g, mask)) < 1e-11
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp64"])
+def test_forces_and_populations_api(storage):
+    nx, ny = 60, 40
+    mask = inputs.inclined_wall_mask(nx, ny, 30.0, 8)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, ny / 2, 8)
+    o, sim, g = run_pair(nx, ny, mask, rA, rB, 17, "improved", storage=storage)
+    rho, rt, F, u = o.fields()
+    tol = 1e-12 if storage == "fp64" else 2e-6
+    np.testing.assert_allclose(sim.forces().cpu().numpy(), F, rtol=0, atol=tol)
+    np.testing.assert_allclose(sim.populations().cpu().numpy(), o.f, rtol=0, atol=tol)
+    m = sim.mass()
+    np.testing.assert_allclose(m, o.mass(), rtol=1e-13 if storage == "fp64" else 1e-6)
+
+
+def test_checkpoint_restore_is_exact():
+    nx, ny = 70, 50
+    mask = inputs.inclined_wall_mask(nx, ny, 10.0, 9)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, ny / 2, 9)
+    a = lbm.Simulation(nx, ny, storage="fp64")
+    a.set_geometry(mask).set_wetting("virtual_avg", G_s=(3.0, 3.0), chi=(1.1, 0.9)).init_fields(rA, rB).step(30)
+    f = a.populations().clone()
+    a.step(20)
+    b = lbm.Simulation(nx, ny, storage="fp64")
+    b.set_geometry(mask).set_wetting("virtual_avg", G_s=(3.0, 3.0), chi=(1.1, 0.9)).set_populations(f).step(20)
+    assert torch.equal(a.populations(), b.populations())
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_deterministic(kernel):
+    nx, ny = 150, 64
+    mask = inputs.inclined_wall_mask(nx, ny, 20.0, 10)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, ny / 2, 10)
+    outs = []
+    for _ in range(2):
+        s = lbm.Simulation(nx, ny, storage="fp32", kernel=kernel)
+        s.set_geometry(mask).set_wetting("improved", G_s=(3.0, 3.0), chi=(1.2, 0.8)).init_fields(rA, rB).step(50)
+        outs.append((s.populations(), s.mass()))
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_interface_count_matches_oracle():
+    nx, ny = 120, 90
+    mask = inputs.circle_surface_mask(nx, ny, 60, 20, 30)
+    sim = lbm.Simulation(nx, ny, periodic_x=True, periodic_y=True)
+    sim.set_geometry(mask)
+    o = oracle.Oracle(nx, ny, mask, periodic_x=True, periodic_y=True)
+    assert sim.interface_count() == int(o.interface_solid().sum())
+
+
+def test_run_host_matches_device_path():
+    nx, ny = 90, 60
+    mask = inputs.inclined_wall_mask(nx, ny, 20.0, 10)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, ny / 2, 10)
+    a = lbm.Simulation(nx, ny)
+    a.set_geometry(mask).set_wetting("llkc", G_s=(-0.5, 0.5)).init_fields(rA, rB).step(40)
+    rhoA, rhoB, u = a.moments()
+    b = lbm.Simulation(nx, ny)
+    outs = [np.zeros((ny, nx)) for _ in range(4)]
+    b.run_host(lbm.make_wetting("llkc", G_s=(-0.5, 0.5)), mask.copy(), rA.copy(), rB.copy(), 40, outs)
+    assert np.array_equal(outs[0], rhoA.cpu().numpy())
+    assert np.array_equal(outs[2], u[0].cpu().numpy())
+
+
+def test_errors_are_status_codes():
+    nx, ny = 16, 16
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Simulation(nx, ny, tau=(0.5, 1.0))
+    assert e.value.status == lbm.ERR_ARG
+    sim = lbm.Simulation(nx, ny)
+    with pytest.raises(lbm.LbmError) as e:
+        sim.step(1)
+    assert e.value.status == lbm.ERR_STATE
+    with pytest.raises(lbm.LbmError) as e:
+        sim.set_geometry(np.zeros((ny, nx), np.uint8))  # fluid on walled borders
+    assert e.value.status == lbm.ERR_ARG
+    with pytest.raises(lbm.LbmError) as e:
+        sim.set_wetting("virtual_avg", chi=(0.0, 1.0))
+    assert e.value.status == lbm.ERR_ARG
+    small = lbm.Simulation(nx, ny, max_interface=3)
+    with pytest.raises(lbm.LbmError) as e:
+        small.set_geometry(inputs.border_walls(nx, ny))
+    assert e.value.status == lbm.ERR_SPACE
