@@ -200,30 +200,75 @@ __device__ __forceinline__ void momentum(const C f[9], C& jx, C& jy) {
   jy = (f[2] - f[4]) + ((f[5] - f[7]) + (f[6] - f[8]));
 }
 
+// Knuth's branch-free two-sum: s + e == a + b exactly.
 template <typename C>
-__device__ __forceinline__ C density(const C f[9]) {
-  return ((f[0] + (f[1] + f[3])) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8]));
+__device__ __forceinline__ C two_sum(C a, C b, C& e) {
+  const C s = a + b;
+  const C bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+  return s;
 }
 
-// BGK relaxation towards Eq. 2 plus the Guo source of Eq. 4, in place.
+// rho = sum_i f_i (Eq. 3). In FP32 the sum is compensated so that rho is
+// (in practice) correctly rounded: the collision conserves mass to within
+// the rounding of rho, and an uncompensated sum leaves a bias that builds up
+// over thousands of steps.
+template <typename C>
+__device__ __forceinline__ C density(const C f[9]) {
+  C e, err = 0;
+  C s = two_sum(f[0], f[1], e);
+  err += e;
+#pragma unroll
+  for (int i = 2; i < 9; ++i) {
+    s = two_sum(s, f[i], e);
+    err += e;
+  }
+  return s + err;
+}
+
+// rho / 9 with one rounding: the product with the two-term split of 1/9.
+// Multiplying by the rounded 1/9 alone makes every weight w_i too large by
+// the same 7.5e-9 (FP32), so sum_i f^eq_i = rho (1 + 7.5e-9) and each
+// collision would add that much mass at every node.
+template <typename C>
+__device__ __forceinline__ C rho_over_9(C rho);
+template <>
+__device__ __forceinline__ float rho_over_9<float>(float rho) {
+  constexpr float HI = (float)(1.0 / 9.0);               // fl(1/9)
+  constexpr float LO = (float)(1.0 / 9.0 - (double)HI);  // 1/9 - fl(1/9)
+  return fmaf(rho, HI, rho * LO);
+}
+template <>
+__device__ __forceinline__ double rho_over_9<double>(double rho) {
+  return rho / 9.0;
+}
+
+// BGK relaxation towards Eq. 2 plus the Guo source of Eq. 4, in place:
+//   f_i <- f_i + omega (f^eq_i - f_i) + S_i,
+// with f^eq_i - f_i evaluated as (rho w_i - f_i) + rho w_i p_i, where p_i =
+// 3 c.u + 4.5 (c.u)^2 - 1.5 u^2 is the small part of Eq. 2's bracket. Each
+// population then takes one rounding at its own magnitude (the final add),
+// and the O(1) part of the bracket is never rounded.
 template <typename C>
 __device__ __forceinline__ void collide(C f[2][9], const C rho[2], C ux, C uy, const C F[2][2],
                                         const C omega[2], const C kF[2]) {
   const C usq15 = C(1.5) * (ux * ux + uy * uy);
+  const C r9[2] = {rho_over_9(rho[0]), rho_over_9(rho[1])};
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const C cu = C(cx_of(i)) * ux + C(cy_of(i)) * uy;
+    const C k = i == 0 ? C(4) : (i <= 4 ? C(1) : C(0.25));  // w_i * 9, exact
+    const C p = C(3) * cu + C(4.5) * cu * cu - usq15;
     const C w = w_of<C>(i);
-    // w_i [1 + 3 cu + 4.5 cu^2 - 1.5 u^2]
-    const C B = w * (C(1) + C(3) * cu + C(4.5) * cu * cu - usq15);
-    // w_i [3 (c_i - u) + 9 (c_i . u) c_i]
+    // w_i [3 (c_i - u) + 9 (c_i . u) c_i]; a common scale error of the weights cancels in sum_i S_i
     const C ex = w * (C(3) * (C(cx_of(i)) - ux) + C(9) * cu * C(cx_of(i)));
     const C ey = w * (C(3) * (C(cy_of(i)) - uy) + C(9) * cu * C(cy_of(i)));
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      const C feq = rho[s] * B;
+      const C ri = k * r9[s];
+      const C d = (ri - f[s][i]) + ri * p;
       const C src = kF[s] * (ex * F[s][0] + ey * F[s][1]);
-      f[s][i] = f[s][i] + omega[s] * (feq - f[s][i]) + src;
+      f[s][i] = f[s][i] + (omega[s] * d + src);
     }
   }
 }

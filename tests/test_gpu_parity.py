@@ -73,7 +73,7 @@ def run_pair(nx, ny, mask, rA, rB, steps, wet, *, periodic=(False, False), stora
 def errors(o, gpu, mask):
     rho, rt, F, u = o.fields()
     fl = mask == 0
-    d_rho = max((np.abs(gpu[0] - rho[0]) / rho[0])[fl].max(), (np.abs(gpu[1] - rho[1]) / rho[1])[fl].max())
+    d_rho = max((np.abs(gpu[0] - rho[0])[fl] / rho[0][fl]).max(), (np.abs(gpu[1] - rho[1])[fl] / rho[1][fl]).max())
     d_u = np.abs(gpu[2] - u)[:, fl].max()
     return d_rho, d_u
 
