@@ -207,6 +207,37 @@ lbm_status lbm_run_host(lbm_ctx* ctx, const lbm_wetting_params* w, const uint8_t
                         double* h_rhoA_out, double* h_rhoB_out, double* h_ux_out,
                         double* h_uy_out);
 
+/* Per-component mass of two density fields without any device allocation
+ * and without a workspace. The paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory at the point they need the
+ * reduction, e.g. code running inside a memory-capped or pre-allocated pool,
+ * or a host thread that must not call cudaMalloc because it would
+ * synchronise the device under work it does not own.
+ *
+ * Computes d_out[0] = sum of d_rhoA, d_out[1] = sum of d_rhoB over the nodes
+ * where d_mask is 0 (all nodes when d_mask is NULL), in FP64 and in a fixed
+ * order (deterministic). d_rhoA, d_rhoB: double [ny][nx]; d_mask: uint8
+ * [ny][nx] or NULL; d_out: 2 doubles; all device pointers owned by the
+ * caller. Enqueued on cuda_stream (NULL = legacy default stream); does not
+ * synchronise.
+ *
+ * Scratch: one partial sum per component and block of 4096 nodes, held in
+ * a 256 KiB file-scope __device__ array that every GPU which loads the
+ * library keeps until the process exits. Hence nx * ny may not exceed
+ * 67,108,864 (8192 * 8192); larger sizes, null pointers and nx or ny < 1
+ * return LBM_ERR_ARG. The array is shared by every call on a device and
+ * keeps the last call's partials (each call overwrites all it reads, so
+ * nothing needs clearing): calls that overlap on the GPU (different streams
+ * without ordering) race and must be serialised by the caller.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. Returns LBM_ERR_CUDA if the lookup or a launch
+ * fails. */
+lbm_status lbm_field_mass_noalloc(const double* d_rhoA, const double* d_rhoB,
+                                  const uint8_t* d_mask, int32_t nx, int32_t ny,
+                                  double* d_out, void* cuda_stream);
+
 /* Release the host context (not the caller's workspace). */
 lbm_status lbm_destroy(lbm_ctx* ctx);
 
