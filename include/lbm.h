@@ -81,8 +81,9 @@ typedef enum {
 
 /* Kernel schedule for lbm_step. TWO_PASS: a density pass, the virtual
  * density pass, then one fused force+collide+stream pull kernel. FUSED: one
- * kernel per step that recomputes densities from the populations of a
- * row window in shared memory (no density array in HBM). AUTO picks FUSED. */
+ * kernel per step that also writes the densities of the next step (the
+ * density plane is double-buffered). AUTO picks the schedule measured
+ * fastest on GB300 (currently TWO_PASS). */
 typedef enum {
   LBM_KERNEL_AUTO = 0,
   LBM_KERNEL_TWO_PASS = 1,

@@ -24,9 +24,13 @@ struct lbm_ctx {
   char* ws;
   size_t ws_bytes;
   void* f[2];          // population buffers (storage type)
-  void* P;             // density plane pair (compute type)
+  void* Pbuf[2];       // two density plane pairs (compute type)
+  void* P;             // Pbuf[pcur]: rho of the current state (when p_valid)
+  int pcur;
+  bool p_valid;        // P holds rho of the current state at fluid nodes
   uint16_t* flags;
   int* iface_list;
+  int* fluid_list;     // bulk fluid nodes, then edge fluid nodes (padded indices)
   int* scan_counts;    // per-block interface counts / offsets
   int* small;          // [0] error count, [1] interface total
   double* partial;     // mass partial sums
@@ -37,6 +41,7 @@ struct lbm_ctx {
   int scan_blocks;
   int mass_blocks;
   int n_iface;
+  int n_fluid;
   int cur;             // index of the buffer holding the current state
   bool has_geometry, has_fields, has_wetting;
   int64_t launches;
@@ -68,7 +73,7 @@ bool make_geo(const lbm_params* p, Geo* g) {
   if (p->nx < 4 || p->ny < 4) return false;
   g->nx = p->nx;
   g->ny = p->ny;
-  g->px = (int)align_up((size_t)p->nx + 2 * GH, 32);
+  g->px = (int)align_up((size_t)LP + p->nx + GH, 32);
   g->py = p->ny + 2 * GH;
   g->plane = (int64_t)g->px * g->py;
   g->per_x = p->periodic_x ? 1 : 0;
@@ -77,7 +82,7 @@ bool make_geo(const lbm_params* p, Geo* g) {
 }
 
 struct Layout {
-  size_t f, P, flags, list, counts, small, partial, mass, smask, stage, total;
+  size_t f, P, flags, list, flist, counts, small, partial, mass, smask, stage, total;
 };
 
 constexpr int MASS_BLOCKS = 1024;
@@ -91,9 +96,10 @@ bool layout(const lbm_params* p, const Geo& g, Layout* L) {
   const int64_t scan_blocks = (N + SCAN_BLOCK - 1) / SCAN_BLOCK;
   size_t off = 0;
   L->f = off;        off = align_up(off + 2 * 18 * (size_t)g.plane * es, A);
-  L->P = off;        off = align_up(off + 2 * (size_t)g.plane * cs, A);
+  L->P = off;        off = align_up(off + 4 * (size_t)g.plane * cs, A);
   L->flags = off;    off = align_up(off + (size_t)g.plane * 2, A);
   L->list = off;     off = align_up(off + (size_t)cap * 4, A);
+  L->flist = off;    off = align_up(off + (size_t)N * 4, A);
   L->counts = off;   off = align_up(off + (size_t)scan_blocks * 4, A);
   L->small = off;    off = align_up(off + 64, A);
   L->partial = off;  off = align_up(off + 2 * MASS_BLOCKS * 8, A);
@@ -142,13 +148,14 @@ lbm_status launch_density_and_virtual(lbm_ctx* c, const T* f) {
   using C = typename Pop<T>::C;
   C* P = (C*)c->P;
   lbm_status s = launch(c, LBM_KC_DENSITY, "k_density", [&] {
-    k_density<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>(f, P, c->flags, c->g, c->ph);
+    k_density<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>(f, P, c->flags, c->g, kphys<C>(c->ph));
   });
   if (s) return s;
+  c->p_valid = (f == (const T*)c->f[c->cur]);
   if (c->ph.bc == BC_VAVG && c->n_iface > 0) {
     s = launch(c, LBM_KC_VIRTUAL, "k_virtual_density", [&] {
       k_virtual_density<C><<<(c->n_iface + 127) / 128, 128, 0, c->stream>>>(P, c->flags, c->iface_list,
-                                                                             c->n_iface, c->g, c->ph);
+                                                                             c->n_iface, c->g, kphys<C>(c->ph));
     });
   }
   return s;
@@ -156,40 +163,67 @@ lbm_status launch_density_and_virtual(lbm_ctx* c, const T* f) {
 
 template <typename T>
 lbm_status step_two_pass(lbm_ctx* c, int nsteps) {
-  for (int t = 0; t < nsteps; ++t) {
+  using C = typename Pop<T>::C;
+  const int nb = (c->n_fluid + 255) / 256;
+  for (int t = 0; t < nsteps && c->n_fluid > 0; ++t) {
     const T* fin = (const T*)c->f[c->cur];
     T* fout = (T*)c->f[c->cur ^ 1];
-    lbm_status s = launch_density_and_virtual<T>(c, fin);
+    C* P = (C*)c->P;
+    lbm_status s = launch(c, LBM_KC_DENSITY, "k_density_list", [&] {
+      k_density_list<T><<<nb, 256, 0, c->stream>>>(fin, P, c->fluid_list, c->n_fluid, c->g, kphys<C>(c->ph));
+    });
     if (s) return s;
-    s = launch(c, LBM_KC_COLLIDE, "k_collide", [&] {
-      k_collide<T, 0><<<node_grid(c->g, 128), 128, 0, c->stream>>>(fin, fout, (const typename Pop<T>::C*)c->P,
-                                                                    c->flags, c->g, c->ph, nullptr);
+    if (c->ph.bc == BC_VAVG && c->n_iface > 0) {
+      s = launch(c, LBM_KC_VIRTUAL, "k_virtual_density", [&] {
+        k_virtual_density<C><<<(c->n_iface + 127) / 128, 128, 0, c->stream>>>(P, c->flags, c->iface_list,
+                                                                               c->n_iface, c->g, kphys<C>(c->ph));
+      });
+      if (s) return s;
+    }
+    s = launch(c, LBM_KC_COLLIDE, "k_collide_list", [&] {
+      k_collide_list<T><<<nb, 256, 0, c->stream>>>(fin, fout, P, c->flags, c->fluid_list, c->n_fluid, c->g,
+                                                  kphys<C>(c->ph));
     });
     if (s) return s;
     c->cur ^= 1;
+    c->p_valid = false;
   }
   return LBM_OK;
 }
 
 template <typename T>
 lbm_status step_fused(lbm_ctx* c, int nsteps) {
+  using C = typename Pop<T>::C;
+  if (nsteps > 0 && !c->p_valid) {
+    // rho of the current state, once; every fused step then produces the next
+    lbm_status s = launch(c, LBM_KC_DENSITY, "k_density", [&] {
+      k_density<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>((const T*)c->f[c->cur], (C*)c->P, c->flags, c->g,
+                                                                  kphys<C>(c->ph));
+    });
+    if (s) return s;
+    c->p_valid = true;
+  }
   for (int t = 0; t < nsteps; ++t) {
     const T* fin = (const T*)c->f[c->cur];
     T* fout = (T*)c->f[c->cur ^ 1];
+    const C* Pin = (const C*)c->Pbuf[c->pcur];
+    C* Pout = (C*)c->Pbuf[c->pcur ^ 1];
     lbm_status ls = LBM_OK;
-    lbm_status s = launch(c, LBM_KC_FUSED, "k_fused", [&] {
-      ls = launch_fused<T>(c->g, c->ph, fin, fout, c->flags, c->num_sms, c->stream);
+    lbm_status s = launch(c, LBM_KC_FUSED, "k_stream", [&] {
+      ls = launch_fused<T>(c->g, c->ph, fin, fout, Pin, Pout, c->flags, c->num_sms, c->stream);
     });
     if (ls) return fail(c, ls, "fused kernel launch rejected");
     if (s) return s;
     c->cur ^= 1;
+    c->pcur ^= 1;
+    c->P = c->Pbuf[c->pcur];
   }
   return LBM_OK;
 }
 
 template <typename T>
 lbm_status do_step(lbm_ctx* c, int nsteps) {
-  const bool fused = c->prm.kernel != LBM_KERNEL_TWO_PASS && fused_supported<T>(c->g, c->ph);
+  const bool fused = c->prm.kernel == LBM_KERNEL_FUSED && fused_supported<T>(c->g, c->ph);
   return fused ? step_fused<T>(c, nsteps) : step_two_pass<T>(c, nsteps);
 }
 
@@ -199,29 +233,31 @@ lbm_status do_eval(lbm_ctx* c, double* out) {
   lbm_status s = launch_density_and_virtual<T>(c, fin);
   if (s) return s;
   k_collide<T, MODE><<<node_grid(c->g, 128), 128, 0, c->stream>>>(fin, nullptr, (const typename Pop<T>::C*)c->P,
-                                                                   c->flags, c->g, c->ph, out);
+                                                                   c->flags, c->g,
+                                                                   kphys<typename Pop<T>::C>(c->ph), out);
   return after_launch(c, "k_collide(eval)");
 }
 
 template <typename T>
 lbm_status do_get_pops(lbm_ctx* c, double* out) {
   k_get_populations<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>((const T*)c->f[c->cur], c->flags, c->g,
-                                                                     c->ph, out);
+                                                                     kphys<typename Pop<T>::C>(c->ph), out);
   return after_launch(c, "k_get_populations");
 }
 
 template <typename T, int SRC>
 lbm_status do_set_state(lbm_ctx* c, const double* fin, const double* rA, const double* rB, const double* ux,
                         const double* uy) {
-  k_set_state<T, SRC><<<node_grid(c->g, 128), 128, 0, c->stream>>>((T*)c->f[c->cur], c->flags, c->g, c->ph,
-                                                                     fin, rA, rB, ux, uy);
+  k_set_state<T, SRC><<<node_grid(c->g, 128), 128, 0, c->stream>>>((T*)c->f[c->cur], c->flags, c->g,
+                                                                     kphys<typename Pop<T>::C>(c->ph), fin, rA, rB,
+                                                                     ux, uy);
   return after_launch(c, "k_set_state");
 }
 
 template <typename T>
 lbm_status do_mass(lbm_ctx* c) {
-  k_mass_partial<T><<<c->mass_blocks, 256, 0, c->stream>>>((const T*)c->f[c->cur], c->flags, c->g, c->ph,
-                                                           c->partial);
+  k_mass_partial<T><<<c->mass_blocks, 256, 0, c->stream>>>((const T*)c->f[c->cur], c->flags, c->g,
+                                                           kphys<typename Pop<T>::C>(c->ph), c->partial);
   lbm_status s = after_launch(c, "k_mass_partial");
   if (s) return s;
   k_mass_final<<<1, 64, 0, c->stream>>>(c->partial, c->mass_blocks, c->mass_out);
@@ -299,9 +335,14 @@ lbm_status lbm_create(const lbm_params* params, void* d_workspace, size_t bytes,
   const size_t es = elem_size(params->storage);
   c->f[0] = c->ws + L.f;
   c->f[1] = c->ws + L.f + 18 * (size_t)g.plane * es;
-  c->P = c->ws + L.P;
+  c->Pbuf[0] = c->ws + L.P;
+  c->Pbuf[1] = c->ws + L.P + 2 * (size_t)g.plane * compute_size(params->storage);
+  c->pcur = 0;
+  c->P = c->Pbuf[0];
+  c->p_valid = false;
   c->flags = (uint16_t*)(c->ws + L.flags);
   c->iface_list = (int*)(c->ws + L.list);
+  c->fluid_list = (int*)(c->ws + L.flist);
   c->scan_counts = (int*)(c->ws + L.counts);
   c->small = (int*)(c->ws + L.small);
   c->partial = (double*)(c->ws + L.partial);
@@ -350,24 +391,34 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* d_mask) {
   if (s) return s;
   k_flags<<<dim3((g.px + 127) / 128, g.py), 128, 0, c->stream>>>(d_mask, c->flags, g, c->small);
   if ((s = after_launch(c, "k_flags"))) return s;
-  k_iface_count<<<c->scan_blocks, SCAN_BLOCK, 0, c->stream>>>(c->flags, g, c->scan_counts);
-  if ((s = after_launch(c, "k_iface_count"))) return s;
-  k_iface_scan<<<1, 1024, 0, c->stream>>>(c->scan_counts, c->scan_blocks, c->small + 1);
-  if ((s = after_launch(c, "k_iface_scan"))) return s;
-  k_iface_write<<<c->scan_blocks, SCAN_BLOCK, 0, c->stream>>>(c->flags, g, c->scan_counts,
-                                                              (int)c->if_capacity, c->iface_list);
-  if ((s = after_launch(c, "k_iface_write"))) return s;
+  // interface-solid list, then the fluid list: bulk nodes first, then edge
+  // nodes (appended after the bulk count, read on the device)
+  const int64_t N = (int64_t)g.nx * g.ny;
+  struct Pass { int cls; int* list; int* total; const int* base; int64_t cap; };
+  const Pass passes[2] = {{CLS_IFACE, c->iface_list, c->small + 1, nullptr, c->if_capacity},
+                          {CLS_FLUID, c->fluid_list, c->small + 2, nullptr, N}};
+  for (const Pass& ps : passes) {
+    k_class_count<<<c->scan_blocks, SCAN_BLOCK, 0, c->stream>>>(c->flags, g, ps.cls, c->scan_counts);
+    if ((s = after_launch(c, "k_class_count"))) return s;
+    k_iface_scan<<<1, 1024, 0, c->stream>>>(c->scan_counts, c->scan_blocks, ps.total);
+    if ((s = after_launch(c, "k_iface_scan"))) return s;
+    k_class_write<<<c->scan_blocks, SCAN_BLOCK, 0, c->stream>>>(c->flags, g, ps.cls, c->scan_counts, ps.base,
+                                                                (int)ps.cap, ps.list);
+    if ((s = after_launch(c, "k_class_write"))) return s;
+  }
   // clear the density planes so solid cells read as zero
-  s = check_cuda(c, cudaMemsetAsync(c->P, 0, 2 * (size_t)g.plane * compute_size(c->prm.storage), c->stream),
+  c->p_valid = false;
+  s = check_cuda(c, cudaMemsetAsync(c->Pbuf[0], 0, 4 * (size_t)g.plane * compute_size(c->prm.storage), c->stream),
                  "cudaMemsetAsync");
   if (s) return s;
-  int h[2];
+  int h[3];
   s = check_cuda(c, cudaMemcpyAsync(h, c->small, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
   if (!s) s = check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   if (s) return s;
   if (h[0] > 0) return fail(c, LBM_ERR_ARG, "fluid node on a non-periodic border");
   if (h[1] > c->if_capacity) return fail(c, LBM_ERR_SPACE, "interface-solid list exceeds max_interface");
   c->n_iface = h[1];
+  c->n_fluid = h[2];
   c->has_geometry = true;
   return LBM_OK;
 }
@@ -396,6 +447,7 @@ lbm_status lbm_init_fields(lbm_ctx* c, const double* rA, const double* rB, const
   if (!c || !rA || !rB) return LBM_ERR_ARG;
   if (!c->has_geometry) return fail(c, LBM_ERR_STATE, "lbm_init_fields before lbm_set_geometry");
   c->cur = 0;
+  c->p_valid = false;
   lbm_status s;
   LBM_DISPATCH(c, s = (do_set_state<T, 1>(c, nullptr, rA, rB, ux, uy)); break);
   if (!s) c->has_fields = true;
@@ -406,6 +458,7 @@ lbm_status lbm_set_populations(lbm_ctx* c, const double* fin) {
   if (!c || !fin) return LBM_ERR_ARG;
   if (!c->has_geometry) return fail(c, LBM_ERR_STATE, "lbm_set_populations before lbm_set_geometry");
   c->cur = 0;
+  c->p_valid = false;
   lbm_status s;
   LBM_DISPATCH(c, s = (do_set_state<T, 0>(c, fin, nullptr, nullptr, nullptr, nullptr)); break);
   if (!s) c->has_fields = true;

@@ -32,12 +32,17 @@ __host__ __device__ constexpr C w_of(int i) {
 // layers cover the widest stencil of the step (Eq. 8's D2Q25 reach of 2 plus
 // the force's reach of 1, plus one for streaming).
 constexpr int GH = 4;
+// Columns of padding left of column 0: more than the ghost layers so that
+// column 0 starts on a 128-byte boundary for 4-byte types (aligned stores of
+// whole rows); the columns beyond the ghost layers count as solid.
+constexpr int LP = 32;
 
 // Per-node flag bits (uint16): bit 0 the node is solid; bit i (1..8) the
 // neighbour x + c_i is solid; bit 9 interface-solid (a solid node with a
 // fluid D2Q9 neighbour).
 constexpr uint16_t F_SOLID = 1u;
 constexpr uint16_t F_IFACE = 1u << 9;
+constexpr uint16_t NB_ANY = 0x1FEu;  // any of the eight neighbours solid
 __host__ __device__ constexpr uint16_t nb_bit(int i) { return uint16_t(1u << i); }
 
 struct Geo {
@@ -45,7 +50,7 @@ struct Geo {
   int px, py;      // padded pitch and rows
   int64_t plane;   // px * py
   int per_x, per_y;
-  __host__ __device__ int idx(int x, int y) const { return (y + GH) * px + (x + GH); }
+  __host__ __device__ int idx(int x, int y) const { return (y + GH) * px + (x + LP); }
 };
 
 // Call fn(k) for every padded index k that holds a periodic image of owned
@@ -90,12 +95,16 @@ struct Pop<float> {
   using C = float;
   static __device__ __forceinline__ float ld(const float* p, int64_t k, float) { return p[k]; }
   static __device__ __forceinline__ void st(float* p, int64_t k, float v, float) { p[k] = v; }
+  static __device__ __forceinline__ float enc(float v, float) { return v; }
+  static __device__ __forceinline__ float dec(float v, float) { return v; }
 };
 template <>
 struct Pop<double> {
   using C = double;
   static __device__ __forceinline__ double ld(const double* p, int64_t k, double) { return p[k]; }
   static __device__ __forceinline__ void st(double* p, int64_t k, double v, double) { p[k] = v; }
+  static __device__ __forceinline__ double enc(double v, double) { return v; }
+  static __device__ __forceinline__ double dec(double v, double) { return v; }
 };
 template <>
 struct Pop<__half> {
@@ -106,6 +115,8 @@ struct Pop<__half> {
   static __device__ __forceinline__ void st(__half* p, int64_t k, float v, float ref) {
     p[k] = __float2half_rn(v - ref);
   }
+  static __device__ __forceinline__ __half enc(float v, float ref) { return __float2half_rn(v - ref); }
+  static __device__ __forceinline__ float dec(__half v, float ref) { return __half2float(v) + ref; }
 };
 template <>
 struct Pop<__nv_bfloat16> {
@@ -116,6 +127,8 @@ struct Pop<__nv_bfloat16> {
   static __device__ __forceinline__ void st(__nv_bfloat16* p, int64_t k, float v, float ref) {
     p[k] = __float2bfloat16_rn(v - ref);
   }
+  static __device__ __forceinline__ __nv_bfloat16 enc(float v, float ref) { return __float2bfloat16_rn(v - ref); }
+  static __device__ __forceinline__ float dec(__nv_bfloat16 v, float ref) { return __bfloat162float(v) + ref; }
 };
 
 // ---------------------------------------------------------------------------
@@ -133,13 +146,57 @@ struct Phys {
   int bc, pairing, avg9;
 };
 
+// The same constants in the arithmetic type of a kernel, converted once on
+// the host (an FP32 kernel then does no FP64 conversions).
+template <typename C>
+struct PhysK {
+  C omega[2], kF[2], G_AB, G_s[2], chi[2], rho_s[2], rho_ref[2];
+  int bc, pairing, avg9;
+};
+
+template <typename C>
+inline PhysK<C> kphys(const Phys& p) {
+  PhysK<C> k;
+  for (int s = 0; s < 2; ++s) {
+    k.omega[s] = C(p.omega[s]);
+    k.kF[s] = C(p.kF[s]);
+    k.G_s[s] = C(p.G_s[s]);
+    k.chi[s] = C(p.chi[s]);
+    k.rho_s[s] = C(p.rho_s[s]);
+    k.rho_ref[s] = C(p.rho_ref[s]);
+  }
+  k.G_AB = C(p.G_AB);
+  k.bc = p.bc;
+  k.pairing = p.pairing;
+  k.avg9 = p.avg9;
+  return k;
+}
+
 // Interaction force on both components at a fluid node (Eq. 5 restricted to
 // fluid neighbours plus Eq. 7). nbP[s][i] is the value of the density plane
 // of component s at x + c_i (the density at fluid nodes, rho~ at interface-
 // solid nodes under the improved scheme); fl holds the neighbour bits.
-template <typename C>
-__device__ __forceinline__ void interaction_force(const Phys& ph, uint16_t fl, const C rho[2],
+// Values at solid neighbours are only read under the improved scheme.
+// BULK_FAST: take the short path when no neighbour is solid (callers that
+// know their whole warp is bulk pass fl = 0; others pass false so that a
+// warp does not split between the two paths).
+template <typename C, bool BULK_FAST = true>
+__device__ __forceinline__ void interaction_force(const PhysK<C>& ph, uint16_t fl, const C rho[2],
                                                   const C nbP[2][9], C F[2][2]) {
+  const C G = ph.G_AB;
+  if (BULK_FAST && !(fl & NB_ANY)) {
+    // bulk node: every neighbour is fluid, Eq. 5 over all eight
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int o = 1 - s;
+      const C* q = nbP[o];
+      const C ax = (q[1] - q[3]) * C(1.0 / 9.0) + ((q[5] - q[7]) + (q[8] - q[6])) * C(1.0 / 36.0);
+      const C ay = (q[2] - q[4]) * C(1.0 / 9.0) + ((q[5] - q[7]) + (q[6] - q[8])) * C(1.0 / 36.0);
+      F[s][0] = -rho[s] * (G * ax);
+      F[s][1] = -rho[s] * (G * ay);
+    }
+    return;
+  }
   C ax[2] = {0, 0}, ay[2] = {0, 0};  // fluid-weighted sums per component
   C sx[2] = {0, 0}, sy[2] = {0, 0};  // solid-weighted sums (improved scheme)
   C vx = 0, vy = 0;                  // sum_i w_i phi_i c_i
@@ -163,7 +220,6 @@ __device__ __forceinline__ void interaction_force(const Phys& ph, uint16_t fl, c
       if (cy_of(i)) vy += cy_of(i) > 0 ? w : -w;
     }
   }
-  const C G = C(ph.G_AB);
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const int o = 1 - s;
@@ -172,7 +228,7 @@ __device__ __forceinline__ void interaction_force(const Phys& ph, uint16_t fl, c
     const bool self = ph.pairing != 0;
     const C rho_c = self ? rho[s] : rho[o];
     const C sx_c = self ? sx[s] : sx[o], sy_c = self ? sy[s] : sy[o];
-    const C rs_c = C(self ? ph.rho_s[s] : ph.rho_s[o]);
+    const C rs_c = self ? ph.rho_s[s] : ph.rho_s[o];
     C bx, by;
     if (ph.bc == BC_MC) {
       bx = vx;
@@ -187,7 +243,7 @@ __device__ __forceinline__ void interaction_force(const Phys& ph, uint16_t fl, c
       bx = rs_c * vx;
       by = rs_c * vy;
     }
-    const C Gs = C(ph.G_s[s]);
+    const C Gs = ph.G_s[s];
     F[s][0] = -rho[s] * (G * ax[o] + Gs * bx);
     F[s][1] = -rho[s] * (G * ay[o] + Gs * by);
   }
@@ -200,30 +256,12 @@ __device__ __forceinline__ void momentum(const C f[9], C& jx, C& jy) {
   jy = (f[2] - f[4]) + ((f[5] - f[7]) + (f[6] - f[8]));
 }
 
-// Knuth's branch-free two-sum: s + e == a + b exactly.
-template <typename C>
-__device__ __forceinline__ C two_sum(C a, C b, C& e) {
-  const C s = a + b;
-  const C bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-  return s;
-}
-
-// rho = sum_i f_i (Eq. 3). In FP32 the sum is compensated so that rho is
-// (in practice) correctly rounded: the collision conserves mass to within
-// the rounding of rho, and an uncompensated sum leaves a bias that builds up
-// over thousands of steps.
+// rho = sum_i f_i (Eq. 3) as a balanced tree. The collision does not rely
+// on rho being correctly rounded: it conserves mass through the rest
+// population (see collide).
 template <typename C>
 __device__ __forceinline__ C density(const C f[9]) {
-  C e, err = 0;
-  C s = two_sum(f[0], f[1], e);
-  err += e;
-#pragma unroll
-  for (int i = 2; i < 9; ++i) {
-    s = two_sum(s, f[i], e);
-    err += e;
-  }
-  return s + err;
+  return ((f[0] + (f[1] + f[3])) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8]));
 }
 
 // rho / 9 with one rounding: the product with the two-term split of 1/9.
@@ -244,32 +282,98 @@ __device__ __forceinline__ double rho_over_9<double>(double rho) {
 }
 
 // BGK relaxation towards Eq. 2 plus the Guo source of Eq. 4, in place:
-//   f_i <- f_i + omega (f^eq_i - f_i) + S_i,
+//   f_i <- f_i + Delta_i,  Delta_i = omega (f^eq_i - f_i) + S_i,
 // with f^eq_i - f_i evaluated as (rho w_i - f_i) + rho w_i p_i, where p_i =
-// 3 c.u + 4.5 (c.u)^2 - 1.5 u^2 is the small part of Eq. 2's bracket. Each
-// population then takes one rounding at its own magnitude (the final add),
-// and the O(1) part of the bracket is never rounded.
+// 3 c.u + 4.5 (c.u)^2 - 1.5 u^2 is the small part of Eq. 2's bracket, so the
+// O(1) part of the bracket is never rounded, and S_i of Eq. 4 written as
+// w_i (1 - 1/(2 tau)) [3 c.F - 3 u.F + 9 (c.u)(c.F)]. The moving populations
+// take their increments and the rest population takes minus their sum:
+// exactly what the method gives (sum_i Delta_i = 0 by Eqs. 2 and 4), and in
+// floating point the mass of each component changes only by the rounding
+// of the nine final additions, whatever the rounding of rho.
 template <typename C>
 __device__ __forceinline__ void collide(C f[2][9], const C rho[2], C ux, C uy, const C F[2][2],
                                         const C omega[2], const C kF[2]) {
   const C usq15 = C(1.5) * (ux * ux + uy * uy);
-  const C r9[2] = {rho_over_9(rho[0]), rho_over_9(rho[1])};
+  C r9[2], r36[2], k9[2], k36[2], uF3[2];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
+  for (int s = 0; s < 2; ++s) {
+    r9[s] = rho_over_9(rho[s]);
+    r36[s] = C(0.25) * r9[s];  // exact
+    k9[s] = kF[s] * C(1.0 / 9.0);
+    k36[s] = kF[s] * C(1.0 / 36.0);
+    uF3[s] = C(3) * (ux * F[s][0] + uy * F[s][1]);
+  }
+  C acc[2] = {0, 0};
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
     const C cu = C(cx_of(i)) * ux + C(cy_of(i)) * uy;
-    const C k = i == 0 ? C(4) : (i <= 4 ? C(1) : C(0.25));  // w_i * 9, exact
-    const C p = C(3) * cu + C(4.5) * cu * cu - usq15;
-    const C w = w_of<C>(i);
-    // w_i [3 (c_i - u) + 9 (c_i . u) c_i]; a common scale error of the weights cancels in sum_i S_i
-    const C ex = w * (C(3) * (C(cx_of(i)) - ux) + C(9) * cu * C(cx_of(i)));
-    const C ey = w * (C(3) * (C(cy_of(i)) - uy) + C(9) * cu * C(cy_of(i)));
+    const C p = cu * (C(3) + C(4.5) * cu) - usq15;
+    const C cu9 = C(9) * cu;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      const C ri = k * r9[s];
+      const C cF = C(cx_of(i)) * F[s][0] + C(cy_of(i)) * F[s][1];
+      const C src = (i <= 4 ? k9[s] : k36[s]) * ((C(3) * cF - uF3[s]) + cu9 * cF);
+      const C ri = i <= 4 ? r9[s] : r36[s];
       const C d = (ri - f[s][i]) + ri * p;
-      const C src = kF[s] * (ex * F[s][0] + ey * F[s][1]);
-      f[s][i] = f[s][i] + (omega[s] * d + src);
+      const C delta = omega[s] * d + src;
+      acc[s] += delta;
+      f[s][i] = f[s][i] + delta;
     }
+  }
+  f[0][0] = f[0][0] - acc[0];
+  f[1][0] = f[1][0] - acc[1];
+}
+
+// Halfway bounce-back done by the writer. When the upstream node x - c_i of
+// fluid node x is solid, what x receives along c_i at the next step is its
+// own post-collision f*_opp(i) (Sec. 2); it is stored in slot i of that solid
+// node (and its periodic images), which no other node writes, so that every
+// pull reads f*_i(x - c_i) without a test.
+template <typename T, typename C>
+__device__ __forceinline__ void store_bounced(T* __restrict__ fo, const Geo& g, int x, int y, uint16_t fl,
+                                              const C fv[2][9], const C ref[2][9]) {
+  if (!(fl & NB_ANY)) return;
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    if (!(fl & nb_bit(opp_of(i)))) continue;
+    int sx = x - cx_of(i), sy = y - cy_of(i);
+    if (g.per_x) sx = (sx + g.nx) % g.nx;
+    if (g.per_y) sy = (sy + g.ny) % g.ny;
+    const int ks = g.idx(sx, sy);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      T* plane = fo + (int64_t)(s * 9 + i) * g.plane;
+      const C v = fv[s][opp_of(i)], r = ref[s][i];
+      Pop<T>::st(plane, ks, v, r);
+      for_ghost_images(g, sx, sy, [&](int kk) { Pop<T>::st(plane, kk, v, r); });
+    }
+  }
+}
+
+// Store the 18 post-collision populations of owned node (x, y) at padded
+// index k, and at its periodic images.
+template <typename T, typename C>
+__device__ __forceinline__ void store_node(T* __restrict__ fo, const Geo& g, int x, int y, int k,
+                                           const C fv[2][9], const C ref[2][9]) {
+  T* p = fo + k;
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      Pop<T>::st(p, 0, fv[s][i], ref[s][i]);
+      p += g.plane;
+    }
+  const bool img = (g.per_x && (x < GH || x >= g.nx - GH)) || (g.per_y && (y < GH || y >= g.ny - GH));
+  if (img) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        T* plane = fo + (int64_t)(s * 9 + i) * g.plane;
+        const C v = fv[s][i], r = ref[s][i];
+        for_ghost_images(g, x, y, [&](int kk) { Pop<T>::st(plane, kk, v, r); });
+      }
   }
 }
 

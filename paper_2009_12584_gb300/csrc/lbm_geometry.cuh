@@ -21,18 +21,21 @@ __device__ __forceinline__ bool solid_at(const uint8_t* __restrict__ mask, const
   return mask[(int64_t)y * g.nx + x] != 0;
 }
 
-// One thread per padded cell. err[0] counts fluid nodes on a walled border.
+// One thread per padded cell. Cells of the ghost layers get the flags of
+// the node they image (periodic axes) or solid (walled axes), neighbour and
+// interface bits included, because the single-pass kernel recomputes
+// densities there. Padding beyond the ghost layers is solid. err[0] counts
+// fluid nodes on a walled border.
 __global__ void k_flags(const uint8_t* __restrict__ mask, uint16_t* __restrict__ flags, Geo g,
                         int* __restrict__ err) {
   const int px = blockIdx.x * blockDim.x + threadIdx.x, py = blockIdx.y;
   if (px >= g.px) return;
-  const int x = px - GH, y = py - GH;
+  const int x = px - LP, y = py - GH;
   const bool owned = x >= 0 && x < g.nx && y >= 0 && y < g.ny;
-  // padding columns beyond nx + GH are outside every stencil; mark solid
   const bool in_halo = x >= -GH && x < g.nx + GH;
   uint16_t fl = 0;
   if (!in_halo || solid_at(mask, g, x, y)) fl |= F_SOLID;
-  if (owned) {
+  if (in_halo) {
     bool any_fluid_nb = false;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
@@ -43,7 +46,7 @@ __global__ void k_flags(const uint8_t* __restrict__ mask, uint16_t* __restrict__
       }
     }
     if ((fl & F_SOLID) && any_fluid_nb) fl |= F_IFACE;
-    if (!(fl & F_SOLID)) {
+    if (owned && !(fl & F_SOLID)) {
       const bool on_wall = (!g.per_x && (x == 0 || x == g.nx - 1)) || (!g.per_y && (y == 0 || y == g.ny - 1));
       if (on_wall) atomicAdd(err, 1);
     }
@@ -53,13 +56,40 @@ __global__ void k_flags(const uint8_t* __restrict__ mask, uint16_t* __restrict__
 
 constexpr int SCAN_BLOCK = 256;
 
-// Pass 1: interface-solid nodes per block of SCAN_BLOCK owned nodes.
-__global__ void __launch_bounds__(SCAN_BLOCK) k_iface_count(const uint16_t* __restrict__ flags, Geo g,
+// Node classes compacted into index lists at set-up (padded indices, node
+// order). IFACE: interface-solid nodes (Eq. 8 is evaluated there). FLUID:
+// every fluid node; its entry carries EDGE_TAG when the node has a solid
+// neighbour or a periodic image in the ghost layers (a "bulk" node has
+// neither). Node order is kept so that neighbouring nodes are updated
+// together and every 32-byte sector is read and written whole.
+enum { CLS_IFACE = 0, CLS_FLUID = 1 };
+constexpr unsigned EDGE_TAG = 0x80000000u;
+
+__device__ __forceinline__ bool has_images(const Geo& g, int x, int y) {
+  return (g.per_x && (x < GH || x >= g.nx - GH)) || (g.per_y && (y < GH || y >= g.ny - GH));
+}
+
+__device__ __forceinline__ bool in_class(const uint16_t* __restrict__ flags, const Geo& g, int64_t n, int cls,
+                                         int* k_out) {
+  const int x = (int)(n % g.nx), y = (int)(n / g.nx);
+  const int k = g.idx(x, y);
+  const uint16_t fl = flags[k];
+  if (cls == CLS_IFACE) {
+    *k_out = k;
+    return fl & F_IFACE;
+  }
+  const bool edge = (fl & NB_ANY) || has_images(g, x, y);
+  *k_out = (int)((unsigned)k | (edge ? EDGE_TAG : 0u));
+  return !(fl & F_SOLID);
+}
+
+// Pass 1: nodes of class cls per block of SCAN_BLOCK owned nodes.
+__global__ void __launch_bounds__(SCAN_BLOCK) k_class_count(const uint16_t* __restrict__ flags, Geo g, int cls,
                                                             int* __restrict__ counts) {
   const int64_t n = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
   const int64_t N = (int64_t)g.nx * g.ny;
-  bool hit = false;
-  if (n < N) hit = flags[g.idx((int)(n % g.nx), (int)(n / g.nx))] & F_IFACE;
+  int k;
+  const bool hit = n < N && in_class(flags, g, n, cls, &k);
   const int c = __syncthreads_count(hit);
   if (threadIdx.x == 0) counts[blockIdx.x] = c;
 }
@@ -100,19 +130,17 @@ __global__ void __launch_bounds__(1024) k_iface_scan(int* __restrict__ counts, i
   if (threadIdx.x == 0) *total = carry;
 }
 
-// Pass 3: write padded indices of interface-solid nodes in node order.
-__global__ void __launch_bounds__(SCAN_BLOCK) k_iface_write(const uint16_t* __restrict__ flags, Geo g,
-                                                            const int* __restrict__ offsets, int capacity,
+// Pass 3: write the padded indices of the nodes of class cls in node order,
+// starting at list[*base] (base may be null: start at 0).
+__global__ void __launch_bounds__(SCAN_BLOCK) k_class_write(const uint16_t* __restrict__ flags, Geo g, int cls,
+                                                            const int* __restrict__ offsets,
+                                                            const int* __restrict__ base, int capacity,
                                                             int* __restrict__ list) {
   __shared__ int warp_base[SCAN_BLOCK / 32];
   const int64_t n = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
   const int64_t N = (int64_t)g.nx * g.ny;
   int k = 0;
-  bool hit = false;
-  if (n < N) {
-    k = g.idx((int)(n % g.nx), (int)(n / g.nx));
-    hit = flags[k] & F_IFACE;
-  }
+  const bool hit = n < N && in_class(flags, g, n, cls, &k);
   const unsigned ball = __ballot_sync(0xffffffffu, hit);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) warp_base[wid] = __popc(ball);
@@ -127,7 +155,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_iface_write(const uint16_t* __re
   }
   __syncthreads();
   if (hit) {
-    const int pos = offsets[blockIdx.x] + warp_base[wid] + __popc(ball & ((1u << lane) - 1u));
+    const int pos = (base ? *base : 0) + offsets[blockIdx.x] + warp_base[wid] + __popc(ball & ((1u << lane) - 1u));
     if (pos < capacity) list[pos] = k;
   }
 }

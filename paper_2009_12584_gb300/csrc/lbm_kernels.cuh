@@ -1,12 +1,14 @@
 // Kernels of the two-pass schedule and the auxiliary kernels (geometry,
 // initialisation, moments, populations, mass). The stored state between
 // steps is the post-collision population f*_i(x) at its source node; a step
-// pulls f_i(x) = f*_i(x - c_i), or f*_{opp(i)}(x) when x - c_i is solid
-// (halfway bounce-back, Sec. 2), which is the post-streaming distribution
-// of Eq. 1, then collides it in place.
+// pulls f_i(x) = f*_i(x - c_i), the post-streaming distribution of Eq. 1,
+// then collides it in place. Halfway bounce-back (Sec. 2) is folded into
+// the state: slot i of a solid node x - c_i holds f*_opp(i)(x), written by x
+// (store_bounced), so the pull needs no test.
 #pragma once
 
 #include "lbm_common.cuh"
+#include "lbm_geometry.cuh"
 
 namespace lbm {
 
@@ -19,22 +21,17 @@ struct Planes {
 
 // Pull the post-streaming populations of both components at padded index k.
 template <typename T, typename C = typename Pop<T>::C>
-__device__ __forceinline__ void gather(const T* __restrict__ f, const Geo& g, int k, uint16_t fl,
-                                       const C ref[2][9], C out[2][9]) {
+__device__ __forceinline__ void gather(const T* __restrict__ f, const Geo& g, int k, const C ref[2][9],
+                                       C out[2][9]) {
 #pragma unroll
   for (int s = 0; s < 2; ++s)
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const int o = opp_of(i);
-      const bool bounce = (i != 0) && (fl & nb_bit(o));
-      const int src = bounce ? k : k - cx_of(i) - cy_of(i) * g.px;
-      const int slot = bounce ? o : i;
-      out[s][i] = Pop<T>::ld(f + (int64_t)(s * 9 + slot) * g.plane, src, bounce ? ref[s][o] : ref[s][i]);
-    }
+    for (int i = 0; i < 9; ++i)
+      out[s][i] = Pop<T>::ld(f + (int64_t)(s * 9 + i) * g.plane, k - cx_of(i) - cy_of(i) * g.px, ref[s][i]);
 }
 
 template <typename C>
-__device__ __forceinline__ void make_refs(const Phys& ph, C ref[2][9]) {
+__device__ __forceinline__ void make_refs(const PhysK<C>& ph, C ref[2][9]) {
 #pragma unroll
   for (int s = 0; s < 2; ++s)
 #pragma unroll
@@ -44,7 +41,8 @@ __device__ __forceinline__ void make_refs(const Phys& ph, C ref[2][9]) {
 // ---- K1: densities --------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(128) k_density(const T* __restrict__ f, typename Pop<T>::C* __restrict__ P,
-                                                 const uint16_t* __restrict__ flags, Geo g, Phys ph) {
+                                                 const uint16_t* __restrict__ flags, Geo g,
+                                                 PhysK<typename Pop<T>::C> ph) {
   using C = typename Pop<T>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= g.nx) return;
@@ -54,41 +52,9 @@ __global__ void __launch_bounds__(128) k_density(const T* __restrict__ f, typena
   C ref[2][9];
   make_refs(ph, ref);
   C fv[2][9];
-  gather<T>(f, g, k, fl, ref, fv);
+  gather<T>(f, g, k, ref, fv);
   put_with_ghosts(P, g, x, y, density(fv[0]));
   put_with_ghosts(P + g.plane, g, x, y, density(fv[1]));
-}
-
-// ---- K2: virtual solid density of Eq. 8 over the interface-solid list -----
-template <typename C>
-__global__ void __launch_bounds__(128) k_virtual_density(C* __restrict__ P, const uint16_t* __restrict__ flags,
-                                                         const int* __restrict__ list, int n, Geo g, Phys ph) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const int k = list[t];
-  const int reach = ph.avg9 ? 1 : 2;
-  C num[2] = {0, 0}, den = 0;
-  for (int dy = -reach; dy <= reach; ++dy)
-    for (int dx = -reach; dx <= reach; ++dx) {
-      if (!(dx | dy)) continue;
-      const int m = k + dx + dy * g.px;
-      if (flags[m] & F_SOLID) continue;
-      const int r2 = dx * dx + dy * dy;
-      C w;
-      if (ph.avg9) {
-        w = r2 == 1 ? C(1) / C(9) : C(1) / C(36);
-      } else {  // D2Q25 weights printed after Eq. 8
-        w = r2 == 1 ? C(4) / C(21)
-                    : r2 == 2 ? C(4) / C(45)
-                              : r2 == 4 ? C(1) / C(60) : r2 == 5 ? C(2) / C(315) : C(1) / C(5040);
-      }
-      num[0] += w * P[m];
-      num[1] += w * P[g.plane + m];
-      den += w;
-    }
-  const int y = k / g.px - GH, x = k % g.px - GH;
-  put_with_ghosts(P, g, x, y, C(ph.chi[0]) * num[0] / den);
-  put_with_ghosts(P + g.plane, g, x, y, C(ph.chi[1]) * num[1] / den);
 }
 
 // Read the density plane at the 8 neighbours of padded index k.
@@ -102,14 +68,165 @@ __device__ __forceinline__ void neighbour_P(const C* __restrict__ P, const Geo& 
   }
 }
 
+// Owned coordinates of padded index k.
+__device__ __forceinline__ void coords(const Geo& g, int k, int& x, int& y) {
+  y = k / g.px - GH;
+  x = k - (y + GH) * g.px - LP;
+}
+
+// ---- K1 over the fluid-node list (node order, edge nodes tagged) ---------
+template <typename T>
+__global__ void __launch_bounds__(256) k_density_list(const T* __restrict__ f, typename Pop<T>::C* __restrict__ P,
+                                                      const int* __restrict__ list, int nfluid, Geo g,
+                                                      PhysK<typename Pop<T>::C> ph) {
+  using C = typename Pop<T>::C;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nfluid) return;
+  const unsigned e = (unsigned)__ldg(list + t);
+  const int k = (int)(e & ~EDGE_TAG);
+  C ref[2][9];
+  make_refs(ph, ref);
+  C fv[2][9];
+  gather<T>(f, g, k, ref, fv);
+  const C r0 = density(fv[0]), r1 = density(fv[1]);
+  P[k] = r0;
+  P[g.plane + k] = r1;
+  if (e & EDGE_TAG) {  // may have periodic images
+    int x, y;
+    coords(g, k, x, y);
+    for_ghost_images(g, x, y, [&](int kk) {
+      P[kk] = r0;
+      P[g.plane + kk] = r1;
+    });
+  }
+}
+
+// ---- K3 over the fluid-node list ------------------------------------------
+// A warp whose 32 nodes are all bulk (eight fluid neighbours, no periodic
+// image) takes a path with no flag load, no adhesion and no bounce-back; any
+// other warp takes the general one for all its nodes.
+template <typename T>
+__global__ void __launch_bounds__(256, 5) k_collide_list(const T* __restrict__ f, T* __restrict__ fo,
+                                                         const typename Pop<T>::C* __restrict__ P,
+                                                         const uint16_t* __restrict__ flags,
+                                                         const int* __restrict__ list, int nfluid, Geo g,
+                                                         PhysK<typename Pop<T>::C> ph) {
+  using C = typename Pop<T>::C;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = t < nfluid;
+  const unsigned e = valid ? (unsigned)__ldg(list + t) : 0u;
+  const bool warp_edge = __any_sync(0xffffffffu, (e & EDGE_TAG) != 0u);
+  if (!valid) return;
+  const int k = (int)(e & ~EDGE_TAG);
+  C ref[2][9];
+  make_refs(ph, ref);
+  C fv[2][9];
+  gather<T>(f, g, k, ref, fv);
+  const C rho[2] = {density(fv[0]), density(fv[1])};
+  C nbP[2][9];
+  neighbour_P(P, g, k, nbP);
+  C F[2][2];
+  uint16_t fl = 0;
+  if (!warp_edge) {
+    interaction_force<C, true>(ph, 0, rho, nbP, F);
+  } else {
+    fl = __ldg(flags + k);
+    interaction_force<C, false>(ph, fl, rho, nbP, F);
+  }
+  C jxA, jyA, jxB, jyB;
+  momentum(fv[0], jxA, jyA);
+  momentum(fv[1], jxB, jyB);
+  const C inv = C(1) / (rho[0] + rho[1]);
+  const C ux = ((jxA + jxB) + C(0.5) * (F[0][0] + F[1][0])) * inv;
+  const C uy = ((jyA + jyB) + C(0.5) * (F[0][1] + F[1][1])) * inv;
+  collide(fv, rho, ux, uy, F, ph.omega, ph.kF);
+  if (!warp_edge) {
+    T* p = fo + k;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        Pop<T>::st(p, 0, fv[s][i], ref[s][i]);
+        p += g.plane;
+      }
+  } else {
+    int x, y;
+    coords(g, k, x, y);
+    store_node(fo, g, x, y, k, fv, ref);
+    store_bounced(fo, g, x, y, fl, fv, ref);
+  }
+}
+
+// ---- K2: virtual solid density of Eq. 8 over the interface-solid list -----
+// All flags and densities of the stencil are loaded in one round trip; the
+// solid neighbours are then dropped by select (their density-plane values
+// are finite: zero or an earlier rho~).
+template <typename C, bool AVG9>
+__device__ __forceinline__ void virtual_density(const C* __restrict__ P, const uint16_t* __restrict__ flags,
+                                                const Geo& g, int k, const PhysK<C>& ph, C& v0, C& v1) {
+  constexpr int REACH = AVG9 ? 1 : 2;
+  constexpr int NB = (2 * REACH + 1) * (2 * REACH + 1);
+  uint16_t fl[NB];
+  C p0[NB], p1[NB];
+#pragma unroll
+  for (int dy = -REACH; dy <= REACH; ++dy)
+#pragma unroll
+    for (int dx = -REACH; dx <= REACH; ++dx) {
+      const int j = (dy + REACH) * (2 * REACH + 1) + (dx + REACH);
+      const int m = k + dx + dy * g.px;
+      fl[j] = __ldg(flags + m);
+      p0[j] = __ldg(P + m);
+      p1[j] = __ldg(P + g.plane + m);
+    }
+  C num0 = 0, num1 = 0, den = 0;
+#pragma unroll
+  for (int dy = -REACH; dy <= REACH; ++dy)
+#pragma unroll
+    for (int dx = -REACH; dx <= REACH; ++dx) {
+      if (dx == 0 && dy == 0) continue;
+      const int j = (dy + REACH) * (2 * REACH + 1) + (dx + REACH);
+      const bool fluid = !(fl[j] & F_SOLID);
+      const int r2 = dx * dx + dy * dy;
+      const C w = AVG9 ? (r2 == 1 ? C(1) / C(9) : C(1) / C(36))
+                       : (r2 == 1   ? C(4) / C(21)
+                          : r2 == 2 ? C(4) / C(45)
+                          : r2 == 4 ? C(1) / C(60)
+                          : r2 == 5 ? C(2) / C(315)
+                                    : C(1) / C(5040));  // D2Q25 weights printed after Eq. 8
+      num0 += fluid ? w * p0[j] : C(0);
+      num1 += fluid ? w * p1[j] : C(0);
+      den += fluid ? w : C(0);
+    }
+  v0 = ph.chi[0] * num0 / den;
+  v1 = ph.chi[1] * num1 / den;
+}
+
+template <typename C>
+__global__ void __launch_bounds__(128) k_virtual_density(C* __restrict__ P, const uint16_t* __restrict__ flags,
+                                                         const int* __restrict__ list, int n, Geo g,
+                                                         PhysK<C> ph) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int k = list[t];
+  C v0, v1;
+  if (ph.avg9)
+    virtual_density<C, true>(P, flags, g, k, ph, v0, v1);
+  else
+    virtual_density<C, false>(P, flags, g, k, ph, v0, v1);
+  int x, y;
+  coords(g, k, x, y);
+  put_with_ghosts(P, g, x, y, v0);
+  put_with_ghosts(P + g.plane, g, x, y, v1);
+}
+
 // ---- K3: fused force + collide + stream (pull) ---------------------------
 // MODE 0: write post-collision populations. MODE 1: write moments (rho, u)
 // instead. MODE 2: write forces.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(128) k_collide(const T* __restrict__ f, T* __restrict__ fo,
                                                  const typename Pop<T>::C* __restrict__ P,
-                                                 const uint16_t* __restrict__ flags, Geo g, Phys ph,
-                                                 double* __restrict__ out) {
+                                                 const uint16_t* __restrict__ flags, Geo g,
+                                                 PhysK<typename Pop<T>::C> ph, double* __restrict__ out) {
   using C = typename Pop<T>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= g.nx) return;
@@ -128,7 +245,7 @@ __global__ void __launch_bounds__(128) k_collide(const T* __restrict__ f, T* __r
   C ref[2][9];
   make_refs(ph, ref);
   C fv[2][9];
-  gather<T>(f, g, k, fl, ref, fv);
+  gather<T>(f, g, k, ref, fv);
   C rho[2] = {density(fv[0]), density(fv[1])};
   C nbP[2][9];
   neighbour_P(P, g, k, nbP);
@@ -157,21 +274,14 @@ __global__ void __launch_bounds__(128) k_collide(const T* __restrict__ f, T* __r
   const C omega[2] = {C(ph.omega[0]), C(ph.omega[1])};
   const C kF[2] = {C(ph.kF[0]), C(ph.kF[1])};
   collide(fv, rho, ux, uy, F, omega, kF);
-#pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      T* plane = fo + (int64_t)(s * 9 + i) * g.plane;
-      const C v = fv[s][i], r = ref[s][i];
-      Pop<T>::st(plane, k, v, r);
-      for_ghost_images(g, x, y, [&](int kk) { Pop<T>::st(plane, kk, v, r); });
-    }
+  store_node(fo, g, x, y, k, fv, ref);
+  store_bounced(fo, g, x, y, fl, fv, ref);
 }
 
 // ---- post-streaming populations out / in ---------------------------------
 template <typename T>
 __global__ void k_get_populations(const T* __restrict__ f, const uint16_t* __restrict__ flags, Geo g,
-                                  Phys ph, double* __restrict__ out) {
+                                  PhysK<typename Pop<T>::C> ph, double* __restrict__ out) {
   using C = typename Pop<T>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= g.nx) return;
@@ -185,7 +295,7 @@ __global__ void k_get_populations(const T* __restrict__ f, const uint16_t* __res
     for (int s = 0; s < 2; ++s)
       for (int i = 0; i < 9; ++i) fv[s][i] = 0;
   } else {
-    gather<T>(f, g, k, fl, ref, fv);
+    gather<T>(f, g, k, ref, fv);
   }
   for (int s = 0; s < 2; ++s)
     for (int i = 0; i < 9; ++i) out[(s * 9 + i) * N + n] = fv[s][i];
@@ -198,12 +308,14 @@ __device__ __forceinline__ int64_t wrap_compact(const Geo& g, int x, int y) {
   return (int64_t)y * g.nx + x;
 }
 
-// State from post-streaming populations: the stored f*_j(y) is the value
+// State from post-streaming populations O: the stored f*_j(y) is the value
 // that streaming delivers to (y + c_j, j), or to (y, opp(j)) when y + c_j
-// is solid. SRC 0: read populations (d_in [2][9][ny][nx]). SRC 1: the
-// populations are the equilibrium of Eq. 2 from rho/u arrays.
+// is solid; and slot i of a solid node x - c_i holds O_i(x) (the bounced
+// value x receives). SRC 0: O is read from fin [2][9][ny][nx]. SRC 1: O is
+// the equilibrium of Eq. 2 of the rho/u arrays.
 template <typename T, int SRC>
-__global__ void k_set_state(T* __restrict__ f, const uint16_t* __restrict__ flags, Geo g, Phys ph,
+__global__ void k_set_state(T* __restrict__ f, const uint16_t* __restrict__ flags, Geo g,
+                            PhysK<typename Pop<T>::C> ph,
                             const double* __restrict__ fin, const double* __restrict__ rA,
                             const double* __restrict__ rB, const double* __restrict__ ux,
                             const double* __restrict__ uy) {
@@ -216,34 +328,41 @@ __global__ void k_set_state(T* __restrict__ f, const uint16_t* __restrict__ flag
   const int64_t N = (int64_t)g.nx * g.ny;
   C ref[2][9];
   make_refs(ph, ref);
+  // O at node m, component s, direction j
+  auto O = [&](int64_t m, int s, int j) -> double {
+    if (SRC == 0) return fin[(s * 9 + j) * N + m];
+    const double r = s ? rB[m] : rA[m];
+    const double vx = ux ? ux[m] : 0.0, vy = uy ? uy[m] : 0.0;
+    const double cu = cx_of(j) * vx + cy_of(j) * vy;
+    return r * w_of<double>(j) * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (vx * vx + vy * vy));
+  };
+  const int64_t n = (int64_t)y * g.nx + x;
+  C fv[2][9];
 #pragma unroll
   for (int s = 0; s < 2; ++s)
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
       const bool bounce = (j != 0) && (fl & nb_bit(j));
-      const int dx = bounce ? 0 : cx_of(j), dy = bounce ? 0 : cy_of(j);
-      const int slot = bounce ? opp_of(j) : j;
-      const int64_t m = wrap_compact(g, x + dx, y + dy);
-      double v;
-      if (SRC == 0) {
-        v = fin[(s * 9 + slot) * N + m];
-      } else {
-        const double r = s ? rB[m] : rA[m];
-        const double vx = ux ? ux[m] : 0.0, vy = uy ? uy[m] : 0.0;
-        const double cu = cx_of(slot) * vx + cy_of(slot) * vy;
-        v = r * w_of<double>(slot) * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (vx * vx + vy * vy));
-      }
-      const C cv = C(v), r = ref[s][j];
-      T* plane = f + (int64_t)(s * 9 + j) * g.plane;
-      Pop<T>::st(plane, k, cv, r);
-      for_ghost_images(g, x, y, [&](int kk) { Pop<T>::st(plane, kk, cv, r); });
+      fv[s][j] = C(bounce ? O(n, s, opp_of(j)) : O(wrap_compact(g, x + cx_of(j), y + cy_of(j)), s, j));
     }
+  store_node(f, g, x, y, k, fv, ref);
+  // the bounced slots: store_bounced writes fv[s][opp(i)] into slot i, so
+  // pass it the received values O_i(x) in the opposite slots
+  if (fl & NB_ANY) {
+    C rv[2][9];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int i = 0; i < 9; ++i) rv[s][opp_of(i)] = C(O(n, s, i));
+    store_bounced(f, g, x, y, fl, rv, ref);
+  }
 }
 
 // ---- FP64 mass: per-block partial sums, then one fixed-order final sum ----
 template <typename T>
 __global__ void __launch_bounds__(256) k_mass_partial(const T* __restrict__ f, const uint16_t* __restrict__ flags,
-                                                      Geo g, Phys ph, double* __restrict__ partial) {
+                                                      Geo g, PhysK<typename Pop<T>::C> ph,
+                                                      double* __restrict__ partial) {
   using C = typename Pop<T>::C;
   __shared__ double red[2][256 / 32];
   C ref[2][9];
