@@ -70,8 +70,10 @@ typedef enum {
 typedef enum { LBM_PAIR_CROSS = 0, LBM_PAIR_SELF = 1 } lbm_pairing;
 
 /* Storage type of the populations. Arithmetic is FP32 for FP32/FP16/BF16
- * and FP64 for FP64. FP16/BF16 store each population as a deviation from
- * w_i times a per-component reference density (see lbm_params). */
+ * and FP64 for FP64. FP16/BF16 store each population as its deviation from
+ * w_i times the density of the node that wrote it (kept in a density plane
+ * of the workspace), so the 16 bits carry the non-equilibrium and velocity
+ * part only. */
 typedef enum {
   LBM_STORE_FP32 = 0,
   LBM_STORE_FP64 = 1,
@@ -98,7 +100,7 @@ typedef struct {
   double G_AB;                /* Shan-Chen strength G_AB = G_BA (Eq. 5) */
   int32_t storage;            /* lbm_storage */
   int32_t kernel;             /* lbm_kernel */
-  double rho_ref[2];          /* FP16/BF16 reference densities (0 -> 1.0) */
+  double rho_ref[2];          /* reserved, ignored (set to 0) */
   int64_t max_interface;      /* capacity of the interface-solid list;
                                  0 -> nx*ny (always enough) */
 } lbm_params;

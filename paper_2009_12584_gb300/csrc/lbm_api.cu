@@ -143,15 +143,19 @@ lbm_status launch(lbm_ctx* c, int cls, const char* where, Fn&& fn) {
 
 dim3 node_grid(const Geo& g, int bx) { return dim3((g.nx + bx - 1) / bx, g.ny); }
 
+// Densities of the current state (and rho~ at interface-solid nodes) into
+// the spare density plane Pbuf[pcur ^ 1]; Pbuf[pcur] keeps the references
+// the current populations were encoded with.
 template <typename T>
 lbm_status launch_density_and_virtual(lbm_ctx* c, const T* f) {
   using C = typename Pop<T>::C;
-  C* P = (C*)c->P;
+  C* P = (C*)c->Pbuf[c->pcur ^ 1];
+  const C* Pref = (const C*)c->Pbuf[c->pcur];
   lbm_status s = launch(c, LBM_KC_DENSITY, "k_density", [&] {
-    k_density<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>(f, P, c->flags, c->g, kphys<C>(c->ph));
+    k_density<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>(f, P, Pref, c->flags, c->g, kphys<C>(c->ph));
   });
   if (s) return s;
-  c->p_valid = (f == (const T*)c->f[c->cur]);
+  c->p_valid = false;
   if (c->ph.bc == BC_VAVG && c->n_iface > 0) {
     s = launch(c, LBM_KC_VIRTUAL, "k_virtual_density", [&] {
       k_virtual_density<C><<<(c->n_iface + 127) / 128, 128, 0, c->stream>>>(P, c->flags, c->iface_list,
@@ -161,6 +165,9 @@ lbm_status launch_density_and_virtual(lbm_ctx* c, const T* f) {
   return s;
 }
 
+// Two-pass step: densities of the pulled populations into the spare plane,
+// rho~ there, then force + collide + stream, whose output is encoded with
+// those densities; the planes then swap roles.
 template <typename T>
 lbm_status step_two_pass(lbm_ctx* c, int nsteps) {
   using C = typename Pop<T>::C;
@@ -168,9 +175,11 @@ lbm_status step_two_pass(lbm_ctx* c, int nsteps) {
   for (int t = 0; t < nsteps && c->n_fluid > 0; ++t) {
     const T* fin = (const T*)c->f[c->cur];
     T* fout = (T*)c->f[c->cur ^ 1];
-    C* P = (C*)c->P;
+    C* P = (C*)c->Pbuf[c->pcur ^ 1];
+    const C* Pref = (const C*)c->Pbuf[c->pcur];
     lbm_status s = launch(c, LBM_KC_DENSITY, "k_density_list", [&] {
-      k_density_list<T><<<nb, 256, 0, c->stream>>>(fin, P, c->fluid_list, c->n_fluid, c->g, kphys<C>(c->ph));
+      k_density_list<T><<<nb, 256, 0, c->stream>>>(fin, P, Pref, c->flags, c->fluid_list, c->n_fluid, c->g,
+                                                  kphys<C>(c->ph));
     });
     if (s) return s;
     if (c->ph.bc == BC_VAVG && c->n_iface > 0) {
@@ -181,11 +190,13 @@ lbm_status step_two_pass(lbm_ctx* c, int nsteps) {
       if (s) return s;
     }
     s = launch(c, LBM_KC_COLLIDE, "k_collide_list", [&] {
-      k_collide_list<T><<<nb, 256, 0, c->stream>>>(fin, fout, P, c->flags, c->fluid_list, c->n_fluid, c->g,
+      k_collide_list<T><<<nb, 256, 0, c->stream>>>(fin, fout, P, Pref, c->flags, c->fluid_list, c->n_fluid, c->g,
                                                   kphys<C>(c->ph));
     });
     if (s) return s;
     c->cur ^= 1;
+    c->pcur ^= 1;
+    c->P = c->Pbuf[c->pcur];
     c->p_valid = false;
   }
   return LBM_OK;
@@ -197,8 +208,8 @@ lbm_status step_fused(lbm_ctx* c, int nsteps) {
   if (nsteps > 0 && !c->p_valid) {
     // rho of the current state, once; every fused step then produces the next
     lbm_status s = launch(c, LBM_KC_DENSITY, "k_density", [&] {
-      k_density<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>((const T*)c->f[c->cur], (C*)c->P, c->flags, c->g,
-                                                                  kphys<C>(c->ph));
+      k_density<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>((const T*)c->f[c->cur], (C*)c->P, (const C*)c->P,
+                                                                  c->flags, c->g, kphys<C>(c->ph));
     });
     if (s) return s;
     c->p_valid = true;
@@ -223,8 +234,10 @@ lbm_status step_fused(lbm_ctx* c, int nsteps) {
 
 template <typename T>
 lbm_status do_step(lbm_ctx* c, int nsteps) {
-  const bool fused = c->prm.kernel == LBM_KERNEL_FUSED && fused_supported<T>(c->g, c->ph);
-  return fused ? step_fused<T>(c, nsteps) : step_two_pass<T>(c, nsteps);
+  if constexpr (sizeof(T) >= 4) {  // the single-pass kernel stores 4- and 8-byte populations only
+    if (c->prm.kernel == LBM_KERNEL_FUSED && fused_supported<T>(c->g, c->ph)) return step_fused<T>(c, nsteps);
+  }
+  return step_two_pass<T>(c, nsteps);
 }
 
 template <typename T, int MODE>
@@ -232,32 +245,34 @@ lbm_status do_eval(lbm_ctx* c, double* out) {
   const T* fin = (const T*)c->f[c->cur];
   lbm_status s = launch_density_and_virtual<T>(c, fin);
   if (s) return s;
-  k_collide<T, MODE><<<node_grid(c->g, 128), 128, 0, c->stream>>>(fin, nullptr, (const typename Pop<T>::C*)c->P,
-                                                                   c->flags, c->g,
-                                                                   kphys<typename Pop<T>::C>(c->ph), out);
+  using C = typename Pop<T>::C;
+  k_collide<T, MODE><<<node_grid(c->g, 128), 128, 0, c->stream>>>(
+      fin, nullptr, (const C*)c->Pbuf[c->pcur ^ 1], (const C*)c->Pbuf[c->pcur], c->flags, c->g, kphys<C>(c->ph), out);
   return after_launch(c, "k_collide(eval)");
 }
 
 template <typename T>
 lbm_status do_get_pops(lbm_ctx* c, double* out) {
-  k_get_populations<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>((const T*)c->f[c->cur], c->flags, c->g,
-                                                                     kphys<typename Pop<T>::C>(c->ph), out);
+  using C = typename Pop<T>::C;
+  k_get_populations<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>((const T*)c->f[c->cur], (const C*)c->P,
+                                                                     c->flags, c->g, kphys<C>(c->ph), out);
   return after_launch(c, "k_get_populations");
 }
 
 template <typename T, int SRC>
 lbm_status do_set_state(lbm_ctx* c, const double* fin, const double* rA, const double* rB, const double* ux,
                         const double* uy) {
-  k_set_state<T, SRC><<<node_grid(c->g, 128), 128, 0, c->stream>>>((T*)c->f[c->cur], c->flags, c->g,
-                                                                     kphys<typename Pop<T>::C>(c->ph), fin, rA, rB,
-                                                                     ux, uy);
+  using C = typename Pop<T>::C;
+  k_set_state<T, SRC><<<node_grid(c->g, 128), 128, 0, c->stream>>>((T*)c->f[c->cur], (C*)c->P, c->flags, c->g,
+                                                                     kphys<C>(c->ph), fin, rA, rB, ux, uy);
   return after_launch(c, "k_set_state");
 }
 
 template <typename T>
 lbm_status do_mass(lbm_ctx* c) {
-  k_mass_partial<T><<<c->mass_blocks, 256, 0, c->stream>>>((const T*)c->f[c->cur], c->flags, c->g,
-                                                           kphys<typename Pop<T>::C>(c->ph), c->partial);
+  using C = typename Pop<T>::C;
+  k_mass_partial<T><<<c->mass_blocks, 256, 0, c->stream>>>((const T*)c->f[c->cur], (const C*)c->P, c->flags,
+                                                           c->g, kphys<C>(c->ph), c->partial);
   lbm_status s = after_launch(c, "k_mass_partial");
   if (s) return s;
   k_mass_final<<<1, 64, 0, c->stream>>>(c->partial, c->mass_blocks, c->mass_out);

@@ -30,17 +30,52 @@ __device__ __forceinline__ void gather(const T* __restrict__ f, const Geo& g, in
       out[s][i] = Pop<T>::ld(f + (int64_t)(s * 9 + i) * g.plane, k - cx_of(i) - cy_of(i) * g.px, ref[s][i]);
 }
 
-template <typename C>
-__device__ __forceinline__ void make_refs(const PhysK<C>& ph, C ref[2][9]) {
+// Encoding references of 16-bit storage. A 2-byte population is stored as
+// its deviation from w_i rho of the node that wrote it, rho being that
+// node's density when it collided (kept in the reference density plane
+// Pref): the deviation is the non-equilibrium and velocity part, a few
+// percent of f, so the 11 (FP16) or 8 (BF16) significand bits go to what
+// varies. For 4- and 8-byte storage the references are not used.
+template <typename T>
+constexpr bool kDev = sizeof(T) == 2;
+
+// References of the 18 populations pulled at padded index k: the writer of
+// slot i is x - c_i, or x itself when x - c_i is solid (its bounced slot).
+// check: whether fl may hold solid neighbours.
+template <typename T, typename C>
+__device__ __forceinline__ void pull_refs(const C* __restrict__ Pref, const Geo& g, int k, uint16_t fl, bool check,
+                                          C ref[2][9]) {
+  if constexpr (kDev<T>) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const bool self = i == 0 || (check && (fl & nb_bit(opp_of(i))));
+        const int m = self ? k : k - cx_of(i) - cy_of(i) * g.px;
+        ref[s][i] = w_of<C>(i) * __ldg(Pref + s * g.plane + m);
+      }
+  } else {
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int i = 0; i < 9; ++i) ref[s][i] = C(0);
+  }
+}
+
+// References for what a node writes (its own slots and its bounced slots):
+// w_i times its own density rho.
+template <typename T, typename C>
+__device__ __forceinline__ void write_refs(const C rho[2], C ref[2][9]) {
 #pragma unroll
   for (int s = 0; s < 2; ++s)
 #pragma unroll
-    for (int i = 0; i < 9; ++i) ref[s][i] = w_of<C>(i) * C(ph.rho_ref[s]);
+    for (int i = 0; i < 9; ++i) ref[s][i] = kDev<T> ? w_of<C>(i) * rho[s] : C(0);
 }
 
 // ---- K1: densities --------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(128) k_density(const T* __restrict__ f, typename Pop<T>::C* __restrict__ P,
+                                                 const typename Pop<T>::C* __restrict__ Pref,
                                                  const uint16_t* __restrict__ flags, Geo g,
                                                  PhysK<typename Pop<T>::C> ph) {
   using C = typename Pop<T>::C;
@@ -50,7 +85,7 @@ __global__ void __launch_bounds__(128) k_density(const T* __restrict__ f, typena
   const uint16_t fl = flags[k];
   if (fl & F_SOLID) return;
   C ref[2][9];
-  make_refs(ph, ref);
+  pull_refs<T>(Pref, g, k, fl, true, ref);
   C fv[2][9];
   gather<T>(f, g, k, ref, fv);
   put_with_ghosts(P, g, x, y, density(fv[0]));
@@ -77,6 +112,8 @@ __device__ __forceinline__ void coords(const Geo& g, int k, int& x, int& y) {
 // ---- K1 over the fluid-node list (node order, edge nodes tagged) ---------
 template <typename T>
 __global__ void __launch_bounds__(256) k_density_list(const T* __restrict__ f, typename Pop<T>::C* __restrict__ P,
+                                                      const typename Pop<T>::C* __restrict__ Pref,
+                                                      const uint16_t* __restrict__ flags,
                                                       const int* __restrict__ list, int nfluid, Geo g,
                                                       PhysK<typename Pop<T>::C> ph) {
   using C = typename Pop<T>::C;
@@ -85,7 +122,12 @@ __global__ void __launch_bounds__(256) k_density_list(const T* __restrict__ f, t
   const unsigned e = (unsigned)__ldg(list + t);
   const int k = (int)(e & ~EDGE_TAG);
   C ref[2][9];
-  make_refs(ph, ref);
+  if constexpr (kDev<T>) {
+    const bool edge = e & EDGE_TAG;
+    pull_refs<T>(Pref, g, k, edge ? __ldg(flags + k) : uint16_t(0), edge, ref);
+  } else {
+    pull_refs<T>(Pref, g, k, 0, false, ref);
+  }
   C fv[2][9];
   gather<T>(f, g, k, ref, fv);
   const C r0 = density(fv[0]), r1 = density(fv[1]);
@@ -108,6 +150,7 @@ __global__ void __launch_bounds__(256) k_density_list(const T* __restrict__ f, t
 template <typename T>
 __global__ void __launch_bounds__(256, 5) k_collide_list(const T* __restrict__ f, T* __restrict__ fo,
                                                          const typename Pop<T>::C* __restrict__ P,
+                                                         const typename Pop<T>::C* __restrict__ Pref,
                                                          const uint16_t* __restrict__ flags,
                                                          const int* __restrict__ list, int nfluid, Geo g,
                                                          PhysK<typename Pop<T>::C> ph) {
@@ -118,19 +161,18 @@ __global__ void __launch_bounds__(256, 5) k_collide_list(const T* __restrict__ f
   const bool warp_edge = __any_sync(0xffffffffu, (e & EDGE_TAG) != 0u);
   if (!valid) return;
   const int k = (int)(e & ~EDGE_TAG);
+  const uint16_t fl = warp_edge ? __ldg(flags + k) : uint16_t(0);
   C ref[2][9];
-  make_refs(ph, ref);
+  pull_refs<T>(Pref, g, k, fl, warp_edge, ref);
   C fv[2][9];
   gather<T>(f, g, k, ref, fv);
   const C rho[2] = {density(fv[0]), density(fv[1])};
   C nbP[2][9];
   neighbour_P(P, g, k, nbP);
   C F[2][2];
-  uint16_t fl = 0;
   if (!warp_edge) {
     interaction_force<C, true>(ph, 0, rho, nbP, F);
   } else {
-    fl = __ldg(flags + k);
     interaction_force<C, false>(ph, fl, rho, nbP, F);
   }
   C jxA, jyA, jxB, jyB;
@@ -140,6 +182,7 @@ __global__ void __launch_bounds__(256, 5) k_collide_list(const T* __restrict__ f
   const C ux = ((jxA + jxB) + C(0.5) * (F[0][0] + F[1][0])) * inv;
   const C uy = ((jyA + jyB) + C(0.5) * (F[0][1] + F[1][1])) * inv;
   collide(fv, rho, ux, uy, F, ph.omega, ph.kF);
+  write_refs<T>(rho, ref);
   if (!warp_edge) {
     T* p = fo + k;
 #pragma unroll
@@ -225,6 +268,7 @@ __global__ void __launch_bounds__(128) k_virtual_density(C* __restrict__ P, cons
 template <typename T, int MODE>
 __global__ void __launch_bounds__(128) k_collide(const T* __restrict__ f, T* __restrict__ fo,
                                                  const typename Pop<T>::C* __restrict__ P,
+                                                 const typename Pop<T>::C* __restrict__ Pref,
                                                  const uint16_t* __restrict__ flags, Geo g,
                                                  PhysK<typename Pop<T>::C> ph, double* __restrict__ out) {
   using C = typename Pop<T>::C;
@@ -243,7 +287,7 @@ __global__ void __launch_bounds__(128) k_collide(const T* __restrict__ f, T* __r
     return;
   }
   C ref[2][9];
-  make_refs(ph, ref);
+  pull_refs<T>(Pref, g, k, fl, true, ref);
   C fv[2][9];
   gather<T>(f, g, k, ref, fv);
   C rho[2] = {density(fv[0]), density(fv[1])};
@@ -274,13 +318,15 @@ __global__ void __launch_bounds__(128) k_collide(const T* __restrict__ f, T* __r
   const C omega[2] = {C(ph.omega[0]), C(ph.omega[1])};
   const C kF[2] = {C(ph.kF[0]), C(ph.kF[1])};
   collide(fv, rho, ux, uy, F, omega, kF);
+  write_refs<T>(rho, ref);
   store_node(fo, g, x, y, k, fv, ref);
   store_bounced(fo, g, x, y, fl, fv, ref);
 }
 
 // ---- post-streaming populations out / in ---------------------------------
 template <typename T>
-__global__ void k_get_populations(const T* __restrict__ f, const uint16_t* __restrict__ flags, Geo g,
+__global__ void k_get_populations(const T* __restrict__ f, const typename Pop<T>::C* __restrict__ Pref,
+                                  const uint16_t* __restrict__ flags, Geo g,
                                   PhysK<typename Pop<T>::C> ph, double* __restrict__ out) {
   using C = typename Pop<T>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
@@ -288,13 +334,13 @@ __global__ void k_get_populations(const T* __restrict__ f, const uint16_t* __res
   const int k = g.idx(x, y);
   const uint16_t fl = flags[k];
   const int64_t n = (int64_t)y * g.nx + x, N = (int64_t)g.nx * g.ny;
-  C ref[2][9];
-  make_refs(ph, ref);
   C fv[2][9];
   if (fl & F_SOLID) {
     for (int s = 0; s < 2; ++s)
       for (int i = 0; i < 9; ++i) fv[s][i] = 0;
   } else {
+    C ref[2][9];
+    pull_refs<T>(Pref, g, k, fl, true, ref);
     gather<T>(f, g, k, ref, fv);
   }
   for (int s = 0; s < 2; ++s)
@@ -313,9 +359,11 @@ __device__ __forceinline__ int64_t wrap_compact(const Geo& g, int x, int y) {
 // is solid; and slot i of a solid node x - c_i holds O_i(x) (the bounced
 // value x receives). SRC 0: O is read from fin [2][9][ny][nx]. SRC 1: O is
 // the equilibrium of Eq. 2 of the rho/u arrays.
+// The node's own post-streaming density is written to Pref as the encoding
+// reference of everything the node stores here.
 template <typename T, int SRC>
-__global__ void k_set_state(T* __restrict__ f, const uint16_t* __restrict__ flags, Geo g,
-                            PhysK<typename Pop<T>::C> ph,
+__global__ void k_set_state(T* __restrict__ f, typename Pop<T>::C* __restrict__ Pref,
+                            const uint16_t* __restrict__ flags, Geo g, PhysK<typename Pop<T>::C> ph,
                             const double* __restrict__ fin, const double* __restrict__ rA,
                             const double* __restrict__ rB, const double* __restrict__ ux,
                             const double* __restrict__ uy) {
@@ -326,8 +374,6 @@ __global__ void k_set_state(T* __restrict__ f, const uint16_t* __restrict__ flag
   const uint16_t fl = flags[k];
   if (fl & F_SOLID) return;
   const int64_t N = (int64_t)g.nx * g.ny;
-  C ref[2][9];
-  make_refs(ph, ref);
   // O at node m, component s, direction j
   auto O = [&](int64_t m, int s, int j) -> double {
     if (SRC == 0) return fin[(s * 9 + j) * N + m];
@@ -337,6 +383,16 @@ __global__ void k_set_state(T* __restrict__ f, const uint16_t* __restrict__ flag
     return r * w_of<double>(j) * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (vx * vx + vy * vy));
   };
   const int64_t n = (int64_t)y * g.nx + x;
+  C rho0[2];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    double r = 0.0;
+    for (int j = 0; j < 9; ++j) r += O(n, s, j);
+    rho0[s] = C(r);
+    put_with_ghosts(Pref + s * g.plane, g, x, y, rho0[s]);
+  }
+  C ref[2][9];
+  write_refs<T>(rho0, ref);
   C fv[2][9];
 #pragma unroll
   for (int s = 0; s < 2; ++s)
@@ -360,19 +416,26 @@ __global__ void k_set_state(T* __restrict__ f, const uint16_t* __restrict__ flag
 
 // ---- FP64 mass: per-block partial sums, then one fixed-order final sum ----
 template <typename T>
-__global__ void __launch_bounds__(256) k_mass_partial(const T* __restrict__ f, const uint16_t* __restrict__ flags,
-                                                      Geo g, PhysK<typename Pop<T>::C> ph,
-                                                      double* __restrict__ partial) {
+__global__ void __launch_bounds__(256) k_mass_partial(const T* __restrict__ f,
+                                                      const typename Pop<T>::C* __restrict__ Pref,
+                                                      const uint16_t* __restrict__ flags, Geo g,
+                                                      PhysK<typename Pop<T>::C> ph, double* __restrict__ partial) {
   using C = typename Pop<T>::C;
   __shared__ double red[2][256 / 32];
-  C ref[2][9];
-  make_refs(ph, ref);
   double acc[2] = {0.0, 0.0};
   const int64_t N = (int64_t)g.nx * g.ny;
   for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
     const int y = (int)(n / g.nx), x = (int)(n % g.nx);
     const int k = g.idx(x, y);
     if (flags[k] & F_SOLID) continue;
+    // a node's own slots were written by the node itself
+    C rw[2] = {C(0), C(0)};
+    if (kDev<T>) {
+      rw[0] = Pref[k];
+      rw[1] = Pref[g.plane + k];
+    }
+    C ref[2][9];
+    write_refs<T>(rw, ref);
     for (int s = 0; s < 2; ++s) {
       double r = 0.0;
       for (int i = 0; i < 9; ++i) r += (double)Pop<T>::ld(f + (int64_t)(s * 9 + i) * g.plane, k, ref[s][i]);

@@ -250,3 +250,42 @@ def test_errors_are_status_codes():
     with pytest.raises(lbm.LbmError) as e:
         small.set_geometry(inputs.border_walls(nx, ny))
     assert e.value.status == lbm.ERR_SPACE
+
+
+# Reduced-precision storage: populations stored as FP16/BF16 deviations from
+# w_i times the density of the node that wrote them (FP32 arithmetic). The
+# bounds below are about 5x the errors measured on GB300 at this size.
+REDUCED_TOL = {"fp16": dict(rho=5e-3, u=2e-4, mass=5e-4), "bf16": dict(rho=0.1, u=2e-3, mass=1e-2)}
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("wet", ["mc", "improved"])
+def test_reduced_storage_inclined_wall(storage, wet):
+    nx, ny = 200, 100
+    mask = inputs.inclined_wall_mask(nx, ny, 20.0, 15)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, ny / 2, 15)
+    o, sim, g = run_pair(nx, ny, mask, rA, rB, 1000, wet, storage=storage)
+    d_rho, d_u = errors(o, g, mask)
+    tol = REDUCED_TOL[storage]
+    assert d_rho <= tol["rho"] and d_u <= tol["u"], (d_rho, d_u)
+    m = sim.mass()
+    assert np.all(np.abs(m - o.mass()) / o.mass() <= tol["mass"]), (m, o.mass())
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_reduced_storage_checkpoint_roundtrip(storage):
+    """Populations written back through lbm_set_populations are re-encoded
+    relative to each node's own density and read back to the precision of
+    the format."""
+    nx, ny = 40, 30
+    mask = inputs.random_solid_mask(nx, ny, seed=5, fraction=0.1)
+    rA, rB, ux, uy = inputs.random_fields(nx, ny, seed=6, lo=0.2, hi=0.9, umax=0.02)
+    a = lbm.Simulation(nx, ny, periodic_x=True, periodic_y=True, storage="fp64")
+    a.set_geometry(mask).set_wetting("llkc", G_s=(-0.5, 0.5)).init_fields(rA, rB, ux, uy).step(5)
+    f = a.populations()
+    b = lbm.Simulation(nx, ny, periodic_x=True, periodic_y=True, storage=storage)
+    b.set_geometry(mask).set_wetting("llkc", G_s=(-0.5, 0.5)).set_populations(f)
+    eps = 2.0 ** -11 if storage == "fp16" else 2.0 ** -8
+    # deviations are a few percent of f at most here
+    err = (b.populations() - f).abs().max().item()
+    assert err <= 0.1 * eps, err
