@@ -241,6 +241,50 @@ lbm_status lbm_field_mass_noalloc(const double* d_rhoA, const double* d_rhoB,
                                   const uint8_t* d_mask, int32_t nx, int32_t ny,
                                   double* d_out, void* cuda_stream);
 
+/* ---- Batched stepping ------------------------------------------------------
+ * Many independent simulations (contexts with their own geometry, wetting
+ * and size, all of the same storage type on one device) advance together:
+ * each step is one launch per kernel class over all of them, and repeated
+ * steps replay a CUDA graph. The batch keeps pointers to the contexts; they
+ * must outlive it, keep their geometry and wetting, and may still be
+ * queried individually (lbm_moments, lbm_mass, ...) between batch steps.
+ * The batch snapshots which members use the improved scheme at creation. */
+typedef struct lbm_batch lbm_batch;
+
+/* Device workspace bytes of a batch over ctxs[0..n). Every member must have
+ * geometry and fields (LBM_ERR_STATE otherwise); all members must share the
+ * storage type and device (LBM_ERR_ARG). */
+lbm_status lbm_batch_workspace_bytes(int32_t n, lbm_ctx* const* ctxs, size_t* bytes);
+
+/* Create a batch on a caller-owned workspace (256-byte aligned) and stream.
+ * Synchronises. */
+lbm_status lbm_batch_create(int32_t n, lbm_ctx* const* ctxs, void* d_workspace, size_t bytes,
+                            void* cuda_stream, lbm_batch** out);
+
+/* Replay steps in CUDA graphs of `steps` steps (even; 0 = launch each step
+ * directly). The graph is built with kernel nodes, not stream capture. */
+lbm_status lbm_batch_set_graph_steps(lbm_batch* b, int32_t steps);
+
+/* Advance every member by nsteps steps. Uploads the members' descriptors
+ * (synchronising on that small copy), then enqueues the work. */
+lbm_status lbm_batch_step(lbm_batch* b, int32_t nsteps);
+
+/* Time the candidate configurations (128 or 256 threads per block for the
+ * density and collide kernels; 2, 8 or 32 steps per graph replay) on the
+ * batch itself, keep the fastest, and write {threads, steps} to h_choice (may
+ * be NULL). Advances every member by the steps it times (about 6 x
+ * trial_steps plus warm-up). */
+lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, int32_t* h_choice);
+
+/* Kernels launched by the batch so far (graph replays count their nodes). */
+int64_t lbm_batch_launch_count(const lbm_batch* b);
+
+/* Text of the last error recorded in the batch ("" if none). */
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+/* Release the batch (not its workspace or members). */
+lbm_status lbm_batch_destroy(lbm_batch* b);
+
 /* Release the host context (not the caller's workspace). */
 lbm_status lbm_destroy(lbm_ctx* ctx);
 

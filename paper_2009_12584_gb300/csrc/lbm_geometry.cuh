@@ -26,7 +26,7 @@ __device__ __forceinline__ bool solid_at(const uint8_t* __restrict__ mask, const
 // interface bits included, because the single-pass kernel recomputes
 // densities there. Padding beyond the ghost layers is solid. err[0] counts
 // fluid nodes on a walled border.
-__global__ void k_flags(const uint8_t* __restrict__ mask, uint16_t* __restrict__ flags, Geo g,
+static __global__ void k_flags(const uint8_t* __restrict__ mask, uint16_t* __restrict__ flags, Geo g,
                         int* __restrict__ err) {
   const int px = blockIdx.x * blockDim.x + threadIdx.x, py = blockIdx.y;
   if (px >= g.px) return;
@@ -84,7 +84,7 @@ __device__ __forceinline__ bool in_class(const uint16_t* __restrict__ flags, con
 }
 
 // Pass 1: nodes of class cls per block of SCAN_BLOCK owned nodes.
-__global__ void __launch_bounds__(SCAN_BLOCK) k_class_count(const uint16_t* __restrict__ flags, Geo g, int cls,
+static __global__ void __launch_bounds__(SCAN_BLOCK) k_class_count(const uint16_t* __restrict__ flags, Geo g, int cls,
                                                             int* __restrict__ counts) {
   const int64_t n = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
   const int64_t N = (int64_t)g.nx * g.ny;
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_class_count(const uint16_t* __re
 }
 
 // Pass 2: exclusive scan of the per-block counts in one block (fixed order).
-__global__ void __launch_bounds__(1024) k_iface_scan(int* __restrict__ counts, int nblocks,
+static __global__ void __launch_bounds__(1024) k_iface_scan(int* __restrict__ counts, int nblocks,
                                                      int* __restrict__ total) {
   __shared__ int carry;
   __shared__ int warp_sums[32];
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(1024) k_iface_scan(int* __restrict__ counts, i
 
 // Pass 3: write the padded indices of the nodes of class cls in node order,
 // starting at list[*base] (base may be null: start at 0).
-__global__ void __launch_bounds__(SCAN_BLOCK) k_class_write(const uint16_t* __restrict__ flags, Geo g, int cls,
+static __global__ void __launch_bounds__(SCAN_BLOCK) k_class_write(const uint16_t* __restrict__ flags, Geo g, int cls,
                                                             const int* __restrict__ offsets,
                                                             const int* __restrict__ base, int capacity,
                                                             int* __restrict__ list) {

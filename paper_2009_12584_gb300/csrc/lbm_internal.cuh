@@ -1,0 +1,54 @@
+// Internal definitions shared by the translation units of the library: the
+// context object behind the opaque lbm_ctx handle.
+#pragma once
+
+#include "lbm.h"
+#include "lbm_fused.cuh"
+#include "lbm_geometry.cuh"
+#include "lbm_kernels.cuh"
+
+using lbm::Geo;
+using lbm::Phys;
+
+struct lbm_ctx {
+  lbm_params prm;
+  Geo g;
+  Phys ph;
+  cudaStream_t stream;
+  int device;
+  int num_sms;
+  // workspace carve-up
+  char* ws;
+  size_t ws_bytes;
+  void* f[2];          // population buffers (storage type)
+  void* Pbuf[2];       // two density plane pairs (compute type)
+  void* P;             // Pbuf[pcur]: the densities the current populations were
+                       // written with (16-bit encoding references); after a
+                       // single-pass step, the densities of the current state
+  int pcur;
+  bool p_valid;        // P holds the densities of the current state (single-pass)
+  uint16_t* flags;
+  int* iface_list;
+  int* fluid_list;     // fluid nodes in node order, edge nodes tagged (padded indices)
+  int* scan_counts;    // per-block interface counts / offsets
+  int* small;          // [0] error count, [1] interface total, [2] fluid total
+  double* partial;     // mass partial sums
+  double* mass_out;    // 2 doubles
+  uint8_t* stage_mask; // lbm_run_host staging
+  double* stage;       // 4 arrays of nx*ny doubles
+  int64_t if_capacity;
+  int scan_blocks;
+  int mass_blocks;
+  int n_iface;
+  int n_fluid;
+  int cur;             // index of the buffer holding the current state
+  bool has_geometry, has_fields, has_wetting;
+  int64_t launches;
+  // lbm_step_profiled: when prof_on, every launch is bracketed by a pair of
+  // events from this pool and tagged with its kernel class
+  bool prof_on;
+  cudaEvent_t* prof_ev;
+  int* prof_cls;
+  int prof_n, prof_cap;
+  char err[512];
+};

@@ -111,14 +111,11 @@ __device__ __forceinline__ void coords(const Geo& g, int k, int& x, int& y) {
 
 // ---- K1 over the fluid-node list (node order, edge nodes tagged) ---------
 template <typename T>
-__global__ void __launch_bounds__(256) k_density_list(const T* __restrict__ f, typename Pop<T>::C* __restrict__ P,
-                                                      const typename Pop<T>::C* __restrict__ Pref,
-                                                      const uint16_t* __restrict__ flags,
-                                                      const int* __restrict__ list, int nfluid, Geo g,
-                                                      PhysK<typename Pop<T>::C> ph) {
+__device__ __forceinline__ void density_node(const T* __restrict__ f, typename Pop<T>::C* __restrict__ P,
+                                             const typename Pop<T>::C* __restrict__ Pref,
+                                             const uint16_t* __restrict__ flags, const int* __restrict__ list, int t,
+                                             const Geo& g) {
   using C = typename Pop<T>::C;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nfluid) return;
   const unsigned e = (unsigned)__ldg(list + t);
   const int k = (int)(e & ~EDGE_TAG);
   C ref[2][9];
@@ -143,19 +140,29 @@ __global__ void __launch_bounds__(256) k_density_list(const T* __restrict__ f, t
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_density_list(const T* __restrict__ f, typename Pop<T>::C* __restrict__ P,
+                                                      const typename Pop<T>::C* __restrict__ Pref,
+                                                      const uint16_t* __restrict__ flags,
+                                                      const int* __restrict__ list, int nfluid, Geo g,
+                                                      PhysK<typename Pop<T>::C> ph) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nfluid) density_node<T>(f, P, Pref, flags, list, t, g);
+}
+
 // ---- K3 over the fluid-node list ------------------------------------------
 // A warp whose 32 nodes are all bulk (eight fluid neighbours, no periodic
 // image) takes a path with no flag load, no adhesion and no bounce-back; any
-// other warp takes the general one for all its nodes.
+// other warp takes the general one for all its nodes. All lanes of the warp
+// must call this (t >= nfluid marks an idle lane).
 template <typename T>
-__global__ void __launch_bounds__(256, 5) k_collide_list(const T* __restrict__ f, T* __restrict__ fo,
-                                                         const typename Pop<T>::C* __restrict__ P,
-                                                         const typename Pop<T>::C* __restrict__ Pref,
-                                                         const uint16_t* __restrict__ flags,
-                                                         const int* __restrict__ list, int nfluid, Geo g,
-                                                         PhysK<typename Pop<T>::C> ph) {
+__device__ __forceinline__ void collide_node(const T* __restrict__ f, T* __restrict__ fo,
+                                             const typename Pop<T>::C* __restrict__ P,
+                                             const typename Pop<T>::C* __restrict__ Pref,
+                                             const uint16_t* __restrict__ flags, const int* __restrict__ list,
+                                             int t, int nfluid, const Geo& g,
+                                             const PhysK<typename Pop<T>::C>& ph) {
   using C = typename Pop<T>::C;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = t < nfluid;
   const unsigned e = valid ? (unsigned)__ldg(list + t) : 0u;
   const bool warp_edge = __any_sync(0xffffffffu, (e & EDGE_TAG) != 0u);
@@ -198,6 +205,16 @@ __global__ void __launch_bounds__(256, 5) k_collide_list(const T* __restrict__ f
     store_node(fo, g, x, y, k, fv, ref);
     store_bounced(fo, g, x, y, fl, fv, ref);
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 5) k_collide_list(const T* __restrict__ f, T* __restrict__ fo,
+                                                         const typename Pop<T>::C* __restrict__ P,
+                                                         const typename Pop<T>::C* __restrict__ Pref,
+                                                         const uint16_t* __restrict__ flags,
+                                                         const int* __restrict__ list, int nfluid, Geo g,
+                                                         PhysK<typename Pop<T>::C> ph) {
+  collide_node<T>(f, fo, P, Pref, flags, list, blockIdx.x * blockDim.x + threadIdx.x, nfluid, g, ph);
 }
 
 // ---- K2: virtual solid density of Eq. 8 over the interface-solid list -----
@@ -245,11 +262,9 @@ __device__ __forceinline__ void virtual_density(const C* __restrict__ P, const u
 }
 
 template <typename C>
-__global__ void __launch_bounds__(128) k_virtual_density(C* __restrict__ P, const uint16_t* __restrict__ flags,
-                                                         const int* __restrict__ list, int n, Geo g,
-                                                         PhysK<C> ph) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
+__device__ __forceinline__ void virtual_density_node(C* __restrict__ P, const uint16_t* __restrict__ flags,
+                                                     const int* __restrict__ list, int t, const Geo& g,
+                                                     const PhysK<C>& ph) {
   const int k = list[t];
   C v0, v1;
   if (ph.avg9)
@@ -261,6 +276,15 @@ __global__ void __launch_bounds__(128) k_virtual_density(C* __restrict__ P, cons
   put_with_ghosts(P, g, x, y, v0);
   put_with_ghosts(P + g.plane, g, x, y, v1);
 }
+
+template <typename C>
+__global__ void __launch_bounds__(128) k_virtual_density(C* __restrict__ P, const uint16_t* __restrict__ flags,
+                                                         const int* __restrict__ list, int n, Geo g,
+                                                         PhysK<C> ph) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) virtual_density_node<C>(P, flags, list, t, g, ph);
+}
+
 
 // ---- K3: fused force + collide + stream (pull) ---------------------------
 // MODE 0: write post-collision populations. MODE 1: write moments (rho, u)
@@ -457,7 +481,7 @@ __global__ void __launch_bounds__(256) k_mass_partial(const T* __restrict__ f,
   }
 }
 
-__global__ void k_mass_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
+static __global__ void k_mass_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
   // one warp per component, fixed lane/stride order, then a fixed shuffle tree
   const int s = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (s >= 2) return;

@@ -191,3 +191,43 @@ def random_solid_mask(nx: int, ny: int, seed: int, fraction: float = 0.2,
     m = (rng.random((ny, nx)) < fraction).astype(np.uint8)
     m |= border_walls(nx, ny, periodic_x, periodic_y)
     return m
+
+
+# Approximate linear maps from a target contact angle (degrees) to the
+# wetting parameter of each scheme, read off flat-wall oracle runs (droplet
+# radius 12, G_AB = 3, densities 1 / 0.055): Martys-Chen and LLKC G_w (with
+# G_As = -G_Bs = G_w), and the improved scheme's xi' with chi = (1 + xi',
+# 1 - xi'). They only spread the synthetic batch over wetting regimes.
+def wetting_for_angle(bc: str, theta_deg: float):
+    d = theta_deg - 90.0
+    if bc == "martys_chen":
+        gw = d / 135.0
+        return dict(G_s=(gw, -gw))
+    if bc == "llkc":
+        gw = d / 37.0
+        return dict(G_s=(gw, -gw))
+    xi = -d / 112.0
+    return dict(G_s=(3.0, 3.0), chi=(1.0 + xi, 1.0 - xi))
+
+
+def batched_workload(n: int = 512, seed: int = 0, size_scale: float = 1.0):
+    """Independent inclined-wall simulations: grid sizes uniform from 64x64
+    to 512x256 (times size_scale), wall angle uniform in [0, 45] degrees,
+    contact angle uniform in [45, 135] degrees, scheme uniform over
+    Martys-Chen, LLKC and the improved virtual density; droplet radius
+    min(nx, ny) / 6, sharp, tangent to the wall."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        nx = int(rng.integers(64, 513) * size_scale)
+        ny = int(rng.integers(64, 257) * size_scale)
+        nx, ny = max(nx, 16), max(ny, 16)
+        beta = float(rng.uniform(0.0, 45.0))
+        theta = float(rng.uniform(45.0, 135.0))
+        bc = ("martys_chen", "llkc", "virtual_avg")[int(rng.integers(0, 3))]
+        R0 = min(nx, ny) / 6.0
+        mask = inclined_wall_mask(nx, ny, beta, R0)
+        rA, rB = sharp_droplet(nx, ny, nx / 2, ny / 2, R0)
+        out.append(dict(nx=nx, ny=ny, beta=beta, theta=theta, bc=bc, wetting=wetting_for_angle(bc, theta),
+                        mask=mask, rhoA=rA, rhoB=rB))
+    return out

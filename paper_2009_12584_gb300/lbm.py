@@ -48,6 +48,8 @@ EXPORTS = [
     "lbm_init_fields", "lbm_step", "lbm_step_profiled", "lbm_moments", "lbm_forces", "lbm_get_populations",
     "lbm_set_populations", "lbm_mass", "lbm_interface_count", "lbm_sync", "lbm_run_host",
     "lbm_destroy", "lbm_status_str", "lbm_last_error", "lbm_launch_count",
+    "lbm_batch_workspace_bytes", "lbm_batch_create", "lbm_batch_set_graph_steps", "lbm_batch_step",
+    "lbm_batch_autotune", "lbm_batch_launch_count", "lbm_batch_last_error", "lbm_batch_destroy",
 ]
 
 _lock = threading.Lock()
@@ -109,6 +111,22 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.lbm_last_error.restype = ctypes.c_char_p
         lib.lbm_launch_count.argtypes = [vp]
         lib.lbm_launch_count.restype = ctypes.c_int64
+        ctxs = ctypes.POINTER(vp)
+        for name, args in {
+            "lbm_batch_workspace_bytes": [i32, ctxs, ctypes.POINTER(ctypes.c_size_t)],
+            "lbm_batch_create": [i32, ctxs, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
+            "lbm_batch_set_graph_steps": [vp, i32],
+            "lbm_batch_step": [vp, i32],
+            "lbm_batch_autotune": [vp, i32, ctypes.POINTER(i32)],
+            "lbm_batch_destroy": [vp],
+        }.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        lib.lbm_batch_launch_count.argtypes = [vp]
+        lib.lbm_batch_launch_count.restype = ctypes.c_int64
+        lib.lbm_batch_last_error.argtypes = [vp]
+        lib.lbm_batch_last_error.restype = ctypes.c_char_p
         _lib = lib
         return lib
 
@@ -269,6 +287,65 @@ class Simulation:
     def close(self):
         if getattr(self, "h", None):
             self.lib.lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent simulations advanced together: one launch per kernel
+    class per step for all of them, replayed from a CUDA graph."""
+
+    def __init__(self, sims, stream=None):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.sims = list(sims)
+        n = len(self.sims)
+        self._arr = (ctypes.c_void_p * n)(*[s.h.value for s in self.sims])
+        nbytes = ctypes.c_size_t()
+        st = self.lib.lbm_batch_workspace_bytes(n, self._arr, ctypes.byref(nbytes))
+        if st:
+            raise LbmError(st, "lbm_batch_workspace_bytes")
+        self.workspace = torch.empty(max(256, nbytes.value), dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = self.lib.lbm_batch_create(n, self._arr, self.workspace.data_ptr(), self.workspace.numel(),
+                                       self.stream.cuda_stream, ctypes.byref(h))
+        if st:
+            raise LbmError(st, "lbm_batch_create")
+        self.h = h
+
+    def _check(self, st, where):
+        if st != OK:
+            raise LbmError(st, where, self.lib.lbm_batch_last_error(self.h).decode())
+
+    def set_graph_steps(self, steps):
+        self._check(self.lib.lbm_batch_set_graph_steps(self.h, int(steps)), "lbm_batch_set_graph_steps")
+        return self
+
+    def step(self, n=1):
+        self._check(self.lib.lbm_batch_step(self.h, int(n)), "lbm_batch_step")
+        return self
+
+    def autotune(self, trial_steps=32):
+        """Pick threads per block and steps per graph replay by timing; the
+        members advance by the timed steps. Returns (threads, steps)."""
+        ch = (ctypes.c_int32 * 2)()
+        self._check(self.lib.lbm_batch_autotune(self.h, int(trial_steps), ch), "lbm_batch_autotune")
+        return int(ch[0]), int(ch[1])
+
+    @property
+    def launch_count(self):
+        return self.lib.lbm_batch_launch_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lbm_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
