@@ -212,6 +212,124 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_single(n, mask, rA, rB, nf, storage, kernel, steps, warmup):
+    """The throughput workload with another population storage."""
+    import torch
+    from paper_2009_12584_gb300 import lbm
+    sim = lbm.Simulation(n, n, periodic_x=True, periodic_y=True, storage=storage, kernel=kernel)
+    sim.set_geometry(mask).set_wetting("virtual_avg", G_s=(3.0, 3.0), chi=chi_from_xi(XI)).init_fields(rA, rB)
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ms_cls, cnt_cls = sim.step_profiled(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    dom = max(ms_cls, key=lambda k: ms_cls[k])
+    per_launch = ms_cls[dom] / max(1, cnt_cls[dom])
+    bpu = BYTES_PER_UPDATE[storage] if dom in ("fused", "collide") else BYTES_PER_UPDATE[storage] // 2
+    pk, _ = peaks()
+    ach = bpu * nf / (per_launch / 1e3) / 1e9
+    out = {"value": round(nf * steps / (t_ms / 1e3) / 1e6, 1), "unit": "MLUPS", "ms_per_step": round(t_ms / steps, 4),
+           "roofline": {"kernel": dom, "achieved": round(ach, 1), "frac": round(ach / pk["hbm_gbs"], 4),
+                        "algorithmic_bytes_per_update": bpu},
+           "kernel_ms_per_step": {k: round(v / steps, 4) for k, v in ms_cls.items() if cnt_cls[k]}}
+    del sim
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(storage, steps, warmup, nsims=512):
+    """512 independent inclined-wall simulations (sizes 64x64 ... 512x256,
+    wall angle 0 ... 45 deg, contact angle 45 ... 135 deg, three schemes mixed,
+    seed 0) advanced together by one batch; steps per graph replay and
+    threads per block picked by the autotuner."""
+    import torch
+    from paper_2009_12584_gb300 import inputs, lbm
+    t0 = time.time()
+    work = inputs.batched_workload(nsims, seed=0)
+    sims = []
+    nf = 0
+    for w in work:
+        s = lbm.Simulation(w["nx"], w["ny"], storage=storage)
+        s.set_geometry(w["mask"]).set_wetting(w["bc"], **w["wetting"]).init_fields(w["rhoA"], w["rhoB"])
+        nf += int((w["mask"] == 0).sum())
+        sims.append(s)
+    b = lbm.Batch(sims)
+    choice = b.autotune(16)
+    b.step(max(warmup, 2))
+    torch.cuda.synchronize()
+    setup = time.time() - t0
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = b.launch_count
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    out = {"value": round(nf * steps / (t_ms / 1e3) / 1e6, 1), "unit": "MLUPS", "ms_per_step": round(t_ms / steps, 4),
+           "sims": nsims, "fluid_nodes": nf, "threads_per_block": choice[0], "steps_per_graph": choice[1],
+           "gpu_launches": b.launch_count - l0, "setup_s": round(setup, 1),
+           "workload": "512 inclined-wall simulations, 64x64..512x256, beta U[0,45], theta U[45,135], "
+                       "MC/LLKC/improved mixed, seed 0"}
+    b.close()
+    del sims, b
+    torch.cuda.empty_cache()
+    return out
+
+
+def accuracy():
+    """Error of FP32/FP16/BF16 storage against the library's FP64 storage
+    (which the parity tests tie to the FP64 oracle to 1e-11): densities and
+    the droplet's sliding velocity on a 200x100 wall inclined at 20 deg after
+    2000 steps (Martys-Chen G_w = -0.2, which slides; improved scheme, which
+    stays at rest), and the equilibrium contact angle of a droplet on a flat
+    wall (160x70, R0 = 24, improved scheme at xi = -0.2, 12000 steps)."""
+    import math
+    import torch
+    from paper_2009_12584_gb300 import diag, inputs, lbm
+    res = {}
+    nx, ny, R0, beta = 200, 100, 15, 20.0
+    mask = inputs.inclined_wall_mask(nx, ny, beta, R0)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, ny / 2, R0)
+    t = (math.cos(math.radians(beta)), math.sin(math.radians(beta)))
+    fl = mask == 0
+    for wet, kw in (("martys_chen", dict(G_s=(-0.2, 0.2))),
+                    ("virtual_avg", dict(G_s=(3.0, 3.0), chi=chi_from_xi(XI)))):
+        runs = {}
+        for st in ("fp64", "fp32", "fp16", "bf16"):
+            sim = lbm.Simulation(nx, ny, storage=st)
+            sim.set_geometry(mask).set_wetting(wet, **kw).init_fields(rA, rB).step(2000)
+            a, b_, u = (v.cpu().numpy() for v in sim.moments())
+            runs[st] = (a, b_, u, diag.com_velocity(a, u, 0.055, t))
+        a0, b0, u0, ud0 = runs["fp64"]
+        for st in ("fp32", "fp16", "bf16"):
+            a, b_, u, ud = runs[st]
+            res[f"{wet}/{st}"] = {
+                "max_rel_rho": float(max((abs(a - a0)[fl] / a0[fl]).max(), (abs(b_ - b0)[fl] / b0[fl]).max())),
+                "max_abs_u": float(abs(u - u0)[:, fl].max()),
+                "sliding_velocity": ud, "sliding_velocity_fp64": ud0, "abs_err_sliding_velocity": abs(ud - ud0)}
+    nx, ny, R0 = 160, 70, 24
+    mask = inputs.flat_wall_mask(nx, ny)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, 1, R0)
+    rA, rB = rA * (1 - mask), rB * (1 - mask)
+    ang = {}
+    for st in ("fp64", "fp32", "fp16", "bf16"):
+        sim = lbm.Simulation(nx, ny, periodic_x=True, storage=st)
+        sim.set_geometry(mask).set_wetting("virtual_avg", G_s=(3.0, 3.0), chi=chi_from_xi(XI)).init_fields(rA, rB)
+        sim.step(12000)
+        a = sim.moments()[0].cpu().numpy()
+        ang[st] = diag.contact_angle(a, mask, (0, 0.5), 0.0)
+    for st in ("fp32", "fp16", "bf16"):
+        res[f"contact_angle/{st}"] = {"theta_deg": ang[st], "theta_fp64_deg": ang["fp64"],
+                                      "abs_err_deg": abs(ang[st] - ang["fp64"])}
+    torch.cuda.empty_cache()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -223,6 +341,7 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=["auto", "two_pass", "fused"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the fp16/bf16, batched and accuracy arms")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -312,6 +431,17 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
 
+    # the other arms of the metric: 16-bit storage and batched simulations
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        del sim
+        torch.cuda.empty_cache()
+        for st in ("fp16", "bf16"):
+            extra[st] = run_single(n, mask, rA, rB, nf, st, args.kernel, args.steps, args.warmup)
+        for st in ("fp32", "fp16"):
+            extra[f"batched_{st}"] = run_batched(st, args.steps, args.warmup)
+        extra["err_vs_fp64"] = accuracy()
+
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
@@ -328,7 +458,7 @@ def main():
                            "all_node_mlups": round(world * n * n * args.steps / (t_ms / 1e3) / 1e6, 1),
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
-                "cpu_baseline": cpu}
+                "cpu_baseline": cpu, **extra}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
