@@ -68,33 +68,39 @@ def _load():
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_LIB_PATH)
-            P = ctypes.POINTER(OracleParams)
-            d = ctypes.POINTER(ctypes.c_double)
-            u8 = ctypes.POINTER(ctypes.c_ubyte)
-            i32 = ctypes.POINTER(ctypes.c_int)
-            lib.oracle_lattice.argtypes = [i32, i32, d, i32]
-            lib.oracle_d2q25.argtypes = [i32, i32, d]
-            lib.oracle_d2q25.restype = ctypes.c_int
-            lib.oracle_check.argtypes = [P, u8]
-            lib.oracle_check.restype = ctypes.c_int
-            lib.oracle_equilibrium.argtypes = [ctypes.c_double] * 3 + [d]
-            lib.oracle_source.argtypes = [ctypes.c_double] * 5 + [d]
-            lib.oracle_densities.argtypes = [P, u8, d, d]
-            lib.oracle_interface_solid.argtypes = [P, u8, u8]
-            lib.oracle_virtual_density.argtypes = [P, u8, d, d]
-            lib.oracle_forces.argtypes = [P, u8, d, d, d]
-            lib.oracle_velocity.argtypes = [P, u8, d, d, d, d]
-            lib.oracle_fields.argtypes = [P, u8, d, d, d, d, d]
-            lib.oracle_collide.argtypes = [P, u8, d, d, d, d, d]
-            lib.oracle_stream.argtypes = [P, u8, d, d]
-            lib.oracle_init.argtypes = [P, u8, d, d, d, d, d]
-            lib.oracle_init.restype = ctypes.c_int
-            lib.oracle_step.argtypes = [P, u8, d, ctypes.c_int]
-            lib.oracle_step.restype = ctypes.c_int
-            lib.oracle_mass.argtypes = [P, u8, d, d]
-            _lib = lib
+            _lib = load_library(_LIB_PATH)
     return _lib
+
+
+def load_library(path):
+    """Open an oracle shared library at ``path`` (the tests also load copies
+    compiled with a planted mistake, to show that the pins catch it)."""
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER(OracleParams)
+    d = ctypes.POINTER(ctypes.c_double)
+    u8 = ctypes.POINTER(ctypes.c_ubyte)
+    i32 = ctypes.POINTER(ctypes.c_int)
+    lib.oracle_lattice.argtypes = [i32, i32, d, i32]
+    lib.oracle_d2q25.argtypes = [i32, i32, d]
+    lib.oracle_d2q25.restype = ctypes.c_int
+    lib.oracle_check.argtypes = [P, u8]
+    lib.oracle_check.restype = ctypes.c_int
+    lib.oracle_equilibrium.argtypes = [ctypes.c_double] * 3 + [d]
+    lib.oracle_source.argtypes = [ctypes.c_double] * 5 + [d]
+    lib.oracle_densities.argtypes = [P, u8, d, d]
+    lib.oracle_interface_solid.argtypes = [P, u8, u8]
+    lib.oracle_virtual_density.argtypes = [P, u8, d, d]
+    lib.oracle_forces.argtypes = [P, u8, d, d, d]
+    lib.oracle_velocity.argtypes = [P, u8, d, d, d, d]
+    lib.oracle_fields.argtypes = [P, u8, d, d, d, d, d]
+    lib.oracle_collide.argtypes = [P, u8, d, d, d, d, d]
+    lib.oracle_stream.argtypes = [P, u8, d, d]
+    lib.oracle_init.argtypes = [P, u8, d, d, d, d, d]
+    lib.oracle_init.restype = ctypes.c_int
+    lib.oracle_step.argtypes = [P, u8, d, ctypes.c_int]
+    lib.oracle_step.restype = ctypes.c_int
+    lib.oracle_mass.argtypes = [P, u8, d, d]
+    return lib
 
 
 def _dp(a: np.ndarray):
@@ -107,9 +113,9 @@ def _mp(m: np.ndarray):
     return m.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
 
 
-def lattice():
+def lattice(lib=None):
     """D2Q9 tables: (cx, cy, w, opp)."""
-    lib = _load()
+    lib = lib or _load()
     cx = np.zeros(9, np.int32)
     cy = np.zeros(9, np.int32)
     w = np.zeros(9)
@@ -120,9 +126,9 @@ def lattice():
     return cx, cy, w, opp
 
 
-def d2q25():
+def d2q25(lib=None):
     """The 24 averaging vectors and weights of Eq. 8: (ex, ey, W)."""
-    lib = _load()
+    lib = lib or _load()
     ex = np.zeros(24, np.int32)
     ey = np.zeros(24, np.int32)
     W = np.zeros(24)
@@ -132,17 +138,17 @@ def d2q25():
     return ex, ey, W
 
 
-def equilibrium(rho: float, ux: float, uy: float) -> np.ndarray:
+def equilibrium(rho: float, ux: float, uy: float, lib=None) -> np.ndarray:
     """Eq. 2 for one component at one node."""
     out = np.zeros(9)
-    _load().oracle_equilibrium(rho, ux, uy, _dp(out))
+    (lib or _load()).oracle_equilibrium(rho, ux, uy, _dp(out))
     return out
 
 
-def source(tau: float, ux: float, uy: float, Fx: float, Fy: float) -> np.ndarray:
+def source(tau: float, ux: float, uy: float, Fx: float, Fy: float, lib=None) -> np.ndarray:
     """Eq. 4 for one component at one node."""
     out = np.zeros(9)
-    _load().oracle_source(tau, ux, uy, Fx, Fy, _dp(out))
+    (lib or _load()).oracle_source(tau, ux, uy, Fx, Fy, _dp(out))
     return out
 
 
@@ -153,8 +159,8 @@ class Oracle:
     def __init__(self, nx, ny, mask, *, tau=(1.0, 1.0), G_AB=3.0,
                  bc=BC_MARTYS_CHEN, G_s=(0.0, 0.0), chi=(1.0, 1.0),
                  rho_s=(0.0, 0.0), pairing=PAIR_CROSS, avg_stencil=25,
-                 periodic_x=False, periodic_y=False):
-        self.lib = _load()
+                 periodic_x=False, periodic_y=False, lib=None):
+        self.lib = lib or _load()
         self.p = OracleParams()
         self.p.nx, self.p.ny = nx, ny
         self.p.periodic_x, self.p.periodic_y = int(periodic_x), int(periodic_y)

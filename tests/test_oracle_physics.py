@@ -1,0 +1,124 @@
+"""Physics pins of the oracle against what the paper prints and what the
+mean-field theory of the model fixes (approximate, stated tolerances):
+
+- flat-interface coexistence: ln(a/b) = G (a - b) for psi = rho (mean field);
+- Laplace law with the surface tension printed in Sec. 4 (sigma = 0.026 at
+  G_AB = 3, read as Delta p = 2 sigma / R, see the design notes);
+- the paper's central observation (Sec. 3): on a staircase wall inclined at
+  20 deg a Martys-Chen or LLKC droplet slides at a speed of order 1e-2, a
+  droplet under the improved virtual-density scheme stays at rest;
+- wetting direction (Sec. 3.1): G_w < 0 wets, G_w = 0 is neutral (90 deg),
+  G_w > 0 does not.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_12584_gb300 import diag, inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_physics.txt")
+
+
+def paper_value(key):
+    for line in open(GOLDEN):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()[:2]
+            if k == key:
+                return float(v)
+    raise KeyError(key)
+
+
+def test_flat_interface_coexistence():
+    G = paper_value("G_AB")
+    nx, ny = 4, 64
+    mask = np.zeros((ny, nx), np.uint8)
+    rA = np.full((ny, nx), 0.055)
+    rA[16:48] = 1.0
+    rB = 1.055 - rA
+    o = oracle.Oracle(nx, ny, mask, periodic_x=True, periodic_y=True, G_AB=G).init(rA, rB).step(4000)
+    rho, _, _, u = o.fields()
+    a, b = rho[0][32, 0], rho[0][0, 0]
+    a2, b2 = rho[1][0, 0], rho[1][32, 0]
+    # symmetric coexistence and the mean-field relation within 5%
+    assert abs(a - a2) < 1e-10 and abs(b - b2) < 1e-10
+    assert abs(math.log(a / b) - G * (a2 - b2)) / (G * (a2 - b2)) < 0.05
+    # the majority/minority ratio is at least 20 at the paper's G
+    assert a / b > 20
+    assert np.abs(u).max() < 1e-5
+
+
+def test_laplace_law_surface_tension():
+    G = paper_value("G_AB")
+    sigma_paper = paper_value("sigma")
+    n = 48
+    mask = np.zeros((n, n), np.uint8)
+    inv_R, dp = [], []
+    for R in (8, 11, 14):
+        rA, rB = inputs.sharp_droplet(n, n, n / 2, n / 2, R, 1.0, 0.055)
+        o = oracle.Oracle(n, n, mask, periodic_x=True, periodic_y=True, G_AB=G).init(rA, rB).step(3000)
+        rho, _, _, _ = o.fields()
+        p = (rho[0] + rho[1]) / 3 + G / 3 * rho[0] * rho[1]  # Eq. 6
+        a, b = rho[0][n // 2, n // 2], rho[0][0, 0]
+        R_eq = math.sqrt((rho[0].sum() - b * n * n) / (a - b) / math.pi)
+        inv_R.append(1 / R_eq)
+        dp.append(p[n // 2, n // 2] - p[0, 0])
+    slope, icpt = np.polyfit(inv_R, dp, 1)
+    # Delta p = 2 sigma / R with the printed sigma, within 10%
+    assert abs(slope / 2 - sigma_paper) / sigma_paper < 0.10, slope
+    assert abs(icpt) < 0.1 * min(dp)
+
+
+def _slide(bc_kw, steps=3000):
+    nx, ny, R0, beta = 80, 60, 10, 20.0
+    mask = inputs.inclined_wall_mask(nx, ny, beta, R0)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, ny / 2, R0)
+    o = oracle.Oracle(nx, ny, mask, **bc_kw).init(rA, rB).step(steps)
+    rho, _, _, u = o.fields()
+    t = (math.cos(math.radians(beta)), math.sin(math.radians(beta)))
+    return diag.com_velocity(rho[0], u, 0.06, t)
+
+
+@pytest.mark.parametrize("kw", [dict(bc=oracle.BC_MARTYS_CHEN, G_s=(-0.2, 0.2)),
+                                dict(bc=oracle.BC_LLKC, G_s=(-0.5, 0.5))], ids=["mc", "llkc"])
+def test_off_grid_wall_droplet_slides(kw):
+    ud = _slide(kw)
+    assert 2e-3 < abs(ud) < 5e-2, ud
+
+
+def test_improved_scheme_droplet_at_rest_on_off_grid_wall():
+    ud = _slide(dict(bc=oracle.BC_VIRTUAL_AVG, G_s=(3.0, 3.0), chi=(1.2, 0.8)))
+    assert abs(ud) < 1e-4, ud
+
+
+def _angle(kw, steps=3000):
+    nx, ny, R0 = 64, 32, 10
+    mask = inputs.flat_wall_mask(nx, ny)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, 1, R0)
+    rA, rB = rA * (1 - mask), rB * (1 - mask)
+    o = oracle.Oracle(nx, ny, mask, periodic_x=True, **kw).init(rA, rB).step(steps)
+    rho, _, _, _ = o.fields()
+    return diag.contact_angle(rho[0], mask, (0, 0.5), 0.0)
+
+
+def test_wetting_direction_martys_chen():
+    wet = _angle(dict(bc=oracle.BC_MARTYS_CHEN, G_s=(-0.2, 0.2)))
+    neutral = _angle(dict(bc=oracle.BC_MARTYS_CHEN, G_s=(0.0, 0.0)))
+    dry = _angle(dict(bc=oracle.BC_MARTYS_CHEN, G_s=(0.2, -0.2)))
+    assert wet < neutral - 15 and dry > neutral + 15, (wet, neutral, dry)
+    assert abs(neutral - 90) < 5, neutral
+    # A <-> B symmetry: G_w and -G_w give supplementary angles (measured
+    # relative to the neutral angle, which absorbs the fit's small bias)
+    assert abs((wet + dry) - 2 * neutral) < 3, (wet, dry, neutral)
+
+
+def test_improved_scheme_neutral_and_supplementary():
+    neutral = _angle(dict(bc=oracle.BC_VIRTUAL_AVG, G_s=(3.0, 3.0), chi=(1.0, 1.0)))
+    a = _angle(dict(bc=oracle.BC_VIRTUAL_AVG, G_s=(3.0, 3.0), chi=(1.2, 0.8)))
+    b = _angle(dict(bc=oracle.BC_VIRTUAL_AVG, G_s=(3.0, 3.0), chi=(0.8, 1.2)))
+    assert abs(neutral - 90) < 5, neutral
+    assert abs((a + b) - 2 * neutral) < 3, (a, b, neutral)
+    # with Eq. 7 as printed, a smaller virtual B density (chi_B < 1) lets A wet
+    assert a < 80, a
