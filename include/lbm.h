@@ -122,7 +122,8 @@ typedef struct lbm_ctx lbm_ctx;
 
 /* Bytes of device workspace a context with these parameters needs.
  * Returns LBM_ERR_ARG for invalid parameters (nx or ny < 4, tau <= 0.5,
- * unknown storage/kernel, a grid whose index space exceeds 2^31). */
+ * unknown storage/kernel, a grid whose padded index space, (nx + 36 rounded
+ * up to a multiple of 32) x (ny + 8), reaches 2^30: about 32,700 x 32,700 nodes). */
 lbm_status lbm_workspace_bytes(const lbm_params* params, size_t* bytes);
 
 /* Create a context on the caller's workspace (device memory of at least

@@ -34,7 +34,7 @@ bool make_geo(const lbm_params* p, Geo* g) {
   g->plane = (int64_t)g->px * g->py;
   g->per_x = p->periodic_x ? 1 : 0;
   g->per_y = p->periodic_y ? 1 : 0;
-  return g->plane < (int64_t(1) << 31) - 64;
+  return g->plane < (int64_t(1) << 30);  // list entries carry two tag bits
 }
 
 struct Layout {
@@ -173,10 +173,19 @@ lbm_status step_fused(lbm_ctx* c, int nsteps) {
   for (int t = 0; t < nsteps; ++t) {
     const T* fin = (const T*)c->f[c->cur];
     T* fout = (T*)c->f[c->cur ^ 1];
-    const C* Pin = (const C*)c->Pbuf[c->pcur];
+    C* Pin = (C*)c->Pbuf[c->pcur];
     C* Pout = (C*)c->Pbuf[c->pcur ^ 1];
+    lbm_status s;
+    if (c->ph.bc == BC_VAVG && c->n_iface > 0) {
+      // rho~(t) of Eq. 8 into the solid cells of the plane the step reads
+      s = launch(c, LBM_KC_VIRTUAL, "k_virtual_density", [&] {
+        k_virtual_density<C><<<(c->n_iface + 127) / 128, 128, 0, c->stream>>>(Pin, c->flags, c->iface_list,
+                                                                               c->n_iface, c->g, kphys<C>(c->ph));
+      });
+      if (s) return s;
+    }
     lbm_status ls = LBM_OK;
-    lbm_status s = launch(c, LBM_KC_FUSED, "k_stream", [&] {
+    s = launch(c, LBM_KC_FUSED, "k_march", [&] {
       ls = launch_fused<T>(c->g, c->ph, fin, fout, Pin, Pout, c->flags, c->num_sms, c->stream);
     });
     if (ls) return fail(c, ls, "fused kernel launch rejected");

@@ -172,14 +172,24 @@ inline PhysK<C> kphys(const Phys& p) {
   return k;
 }
 
+// sum_i w_i c_i q_i over the eight moving directions, as paired
+// differences (q[0] unused).
+template <typename C>
+__device__ __forceinline__ void weighted_sum(const C q[9], C& sx, C& sy) {
+  sx = (q[1] - q[3]) * C(1.0 / 9.0) + ((q[5] - q[7]) + (q[8] - q[6])) * C(1.0 / 36.0);
+  sy = (q[2] - q[4]) * C(1.0 / 9.0) + ((q[5] - q[7]) + (q[6] - q[8])) * C(1.0 / 36.0);
+}
+
 // Interaction force on both components at a fluid node (Eq. 5 restricted to
 // fluid neighbours plus Eq. 7). nbP[s][i] is the value of the density plane
 // of component s at x + c_i (the density at fluid nodes, rho~ at interface-
 // solid nodes under the improved scheme); fl holds the neighbour bits.
-// Values at solid neighbours are only read under the improved scheme.
+// Values at solid neighbours are only used under the improved scheme.
 // BULK_FAST: take the short path when no neighbour is solid (callers that
 // know their whole warp is bulk pass fl = 0; others pass false so that a
-// warp does not split between the two paths).
+// warp does not split between the two paths). The general path splits the
+// neighbour values by select into a fluid and a solid part and sums each
+// with the bulk formula.
 template <typename C, bool BULK_FAST = true>
 __device__ __forceinline__ void interaction_force(const PhysK<C>& ph, uint16_t fl, const C rho[2],
                                                   const C nbP[2][9], C F[2][2]) {
@@ -188,38 +198,32 @@ __device__ __forceinline__ void interaction_force(const PhysK<C>& ph, uint16_t f
     // bulk node: every neighbour is fluid, Eq. 5 over all eight
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      const int o = 1 - s;
-      const C* q = nbP[o];
-      const C ax = (q[1] - q[3]) * C(1.0 / 9.0) + ((q[5] - q[7]) + (q[8] - q[6])) * C(1.0 / 36.0);
-      const C ay = (q[2] - q[4]) * C(1.0 / 9.0) + ((q[5] - q[7]) + (q[6] - q[8])) * C(1.0 / 36.0);
+      C ax, ay;
+      weighted_sum(nbP[1 - s], ax, ay);
       F[s][0] = -rho[s] * (G * ax);
       F[s][1] = -rho[s] * (G * ay);
     }
     return;
   }
-  C ax[2] = {0, 0}, ay[2] = {0, 0};  // fluid-weighted sums per component
+  C ax[2], ay[2];                    // fluid-weighted sums per component
   C sx[2] = {0, 0}, sy[2] = {0, 0};  // solid-weighted sums (improved scheme)
-  C vx = 0, vy = 0;                  // sum_i w_i phi_i c_i
+  C qf[9], qs[9], b[9];
+  qf[0] = qs[0] = b[0] = C(0);
 #pragma unroll
-  for (int i = 1; i < 9; ++i) {
-    const C w = w_of<C>(i);
-    const bool solid = fl & nb_bit(i);
+  for (int s = 0; s < 2; ++s) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const C wv = w * nbP[s][i];
-      if (!solid) {
-        if (cx_of(i)) ax[s] += cx_of(i) > 0 ? wv : -wv;
-        if (cy_of(i)) ay[s] += cy_of(i) > 0 ? wv : -wv;
-      } else {
-        if (cx_of(i)) sx[s] += cx_of(i) > 0 ? wv : -wv;
-        if (cy_of(i)) sy[s] += cy_of(i) > 0 ? wv : -wv;
-      }
+    for (int i = 1; i < 9; ++i) {
+      const bool solid = fl & nb_bit(i);
+      qf[i] = solid ? C(0) : nbP[s][i];
+      qs[i] = solid ? nbP[s][i] : C(0);
     }
-    if (solid) {
-      if (cx_of(i)) vx += cx_of(i) > 0 ? w : -w;
-      if (cy_of(i)) vy += cy_of(i) > 0 ? w : -w;
-    }
+    weighted_sum(qf, ax[s], ay[s]);
+    if (ph.bc == BC_VAVG) weighted_sum(qs, sx[s], sy[s]);
   }
+#pragma unroll
+  for (int i = 1; i < 9; ++i) b[i] = (fl & nb_bit(i)) ? C(1) : C(0);
+  C vx, vy;  // sum_i w_i phi(x + c_i) c_i
+  weighted_sum(b, vx, vy);
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const int o = 1 - s;
@@ -348,6 +352,22 @@ __device__ __forceinline__ void store_bounced(T* __restrict__ fo, const Geo& g, 
       Pop<T>::st(plane, ks, v, r);
       for_ghost_images(g, sx, sy, [&](int kk) { Pop<T>::st(plane, kk, v, r); });
     }
+  }
+}
+
+// store_bounced for a node that is not within GH + 1 of a periodic border:
+// its solid neighbours are owned nodes without images, at padded index
+// k - c_i.
+template <typename T, typename C>
+__device__ __forceinline__ void store_bounced_near(T* __restrict__ fo, const Geo& g, int k, uint16_t fl,
+                                                   const C fv[2][9], const C ref[2][9]) {
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    if (!(fl & nb_bit(opp_of(i)))) continue;
+    const int ks = k - cx_of(i) - cy_of(i) * g.px;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+      Pop<T>::st(fo + (int64_t)(s * 9 + i) * g.plane, ks, fv[s][opp_of(i)], ref[s][i]);
   }
 }
 

@@ -58,15 +58,20 @@ constexpr int SCAN_BLOCK = 256;
 
 // Node classes compacted into index lists at set-up (padded indices, node
 // order). IFACE: interface-solid nodes (Eq. 8 is evaluated there). FLUID:
-// every fluid node; its entry carries EDGE_TAG when the node has a solid
-// neighbour or a periodic image in the ghost layers (a "bulk" node has
-// neither). Node order is kept so that neighbouring nodes are updated
-// together and every 32-byte sector is read and written whole.
+// every fluid node, its entry tagged in the two top bits. BORDER_TAG: the
+// node lies within GH + 1 of a periodic border, so that it or one of its
+// D2Q9 neighbours has periodic images in the ghost layers. EDGE_TAG: the
+// node has a solid neighbour or carries BORDER_TAG. A "bulk" node has
+// neither tag. Node order is kept so that neighbouring nodes are updated
+// together and every 32-byte sector is read and written whole. Padded
+// indices stay below 2^30, which leaves the two top bits free.
 enum { CLS_IFACE = 0, CLS_FLUID = 1 };
 constexpr unsigned EDGE_TAG = 0x80000000u;
+constexpr unsigned BORDER_TAG = 0x40000000u;
+constexpr unsigned LIST_TAGS = EDGE_TAG | BORDER_TAG;
 
-__device__ __forceinline__ bool has_images(const Geo& g, int x, int y) {
-  return (g.per_x && (x < GH || x >= g.nx - GH)) || (g.per_y && (y < GH || y >= g.ny - GH));
+__device__ __forceinline__ bool near_border(const Geo& g, int x, int y) {
+  return (g.per_x && (x <= GH || x >= g.nx - GH - 1)) || (g.per_y && (y <= GH || y >= g.ny - GH - 1));
 }
 
 __device__ __forceinline__ bool in_class(const uint16_t* __restrict__ flags, const Geo& g, int64_t n, int cls,
@@ -78,8 +83,9 @@ __device__ __forceinline__ bool in_class(const uint16_t* __restrict__ flags, con
     *k_out = k;
     return fl & F_IFACE;
   }
-  const bool edge = (fl & NB_ANY) || has_images(g, x, y);
-  *k_out = (int)((unsigned)k | (edge ? EDGE_TAG : 0u));
+  const bool border = near_border(g, x, y);
+  const bool edge = (fl & NB_ANY) || border;
+  *k_out = (int)((unsigned)k | (edge ? EDGE_TAG : 0u) | (border ? BORDER_TAG : 0u));
   return !(fl & F_SOLID);
 }
 

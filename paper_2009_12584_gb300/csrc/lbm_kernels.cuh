@@ -9,6 +9,7 @@
 
 #include "lbm_common.cuh"
 #include "lbm_geometry.cuh"
+#include "lbm_pair.cuh"
 
 namespace lbm {
 
@@ -117,7 +118,7 @@ __device__ __forceinline__ void density_node(const T* __restrict__ f, typename P
                                              const Geo& g) {
   using C = typename Pop<T>::C;
   const unsigned e = (unsigned)__ldg(list + t);
-  const int k = (int)(e & ~EDGE_TAG);
+  const int k = (int)(e & ~LIST_TAGS);
   C ref[2][9];
   if constexpr (kDev<T>) {
     const bool edge = e & EDGE_TAG;
@@ -130,7 +131,7 @@ __device__ __forceinline__ void density_node(const T* __restrict__ f, typename P
   const C r0 = density(fv[0]), r1 = density(fv[1]);
   P[k] = r0;
   P[g.plane + k] = r1;
-  if (e & EDGE_TAG) {  // may have periodic images
+  if (e & BORDER_TAG) {  // may have periodic images
     int x, y;
     coords(g, k, x, y);
     for_ghost_images(g, x, y, [&](int kk) {
@@ -150,11 +151,71 @@ __global__ void __launch_bounds__(256) k_density_list(const T* __restrict__ f, t
   if (t < nfluid) density_node<T>(f, P, Pref, flags, list, t, g);
 }
 
+// The update of collide_node for the FP32 compute type, with the two
+// components as float2 pairs (lbm_pair.cuh). Same paths, same stores.
+template <typename T>
+__device__ __forceinline__ void collide_node_pair(const T* __restrict__ f, T* __restrict__ fo,
+                                                  const float* __restrict__ P, const float* __restrict__ Pref,
+                                                  const uint16_t* __restrict__ flags, unsigned e, bool warp_edge,
+                                                  bool warp_border, const Geo& g, const PhysK<float>& ph) {
+  const int k = (int)(e & ~LIST_TAGS);
+  const uint16_t fl = warp_edge ? __ldg(flags + k) : uint16_t(0);
+  float ref[2][9];
+  pull_refs<T>(Pref, g, k, fl, warp_edge, ref);
+  float2 fp[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int m = k - cx_of(i) - cy_of(i) * g.px;
+    fp[i] = f2(Pop<T>::ld(f + (int64_t)i * g.plane, m, ref[0][i]),
+               Pop<T>::ld(f + (int64_t)(9 + i) * g.plane, m, ref[1][i]));
+  }
+  float2 q[9];
+  q[0] = f2(0.0f);
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const int m = k + cx_of(i) + cy_of(i) * g.px;
+    q[i] = f2(__ldg(P + m), __ldg(P + g.plane + m));
+  }
+  const float2 rho = warp_edge ? update_pair<true>(fp, q, fl, ph) : update_pair<false>(fp, q, fl, ph);
+  const float rr[2] = {rho.x, rho.y};
+  write_refs<T>(rr, ref);
+  if (!warp_border) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      Pop<T>::st(fo + (int64_t)i * g.plane, k, fp[i].x, ref[0][i]);
+      Pop<T>::st(fo + (int64_t)(9 + i) * g.plane, k, fp[i].y, ref[1][i]);
+    }
+    if (warp_edge) {
+#pragma unroll
+      for (int i = 1; i < 9; ++i) {
+        if (!(fl & nb_bit(opp_of(i)))) continue;
+        const int ks = k - cx_of(i) - cy_of(i) * g.px;
+        Pop<T>::st(fo + (int64_t)i * g.plane, ks, fp[opp_of(i)].x, ref[0][i]);
+        Pop<T>::st(fo + (int64_t)(9 + i) * g.plane, ks, fp[opp_of(i)].y, ref[1][i]);
+      }
+    }
+  } else {
+    float fv[2][9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      fv[0][i] = fp[i].x;
+      fv[1][i] = fp[i].y;
+    }
+    int x, y;
+    coords(g, k, x, y);
+    store_node(fo, g, x, y, k, fv, ref);
+    store_bounced(fo, g, x, y, fl, fv, ref);
+  }
+}
+
 // ---- K3 over the fluid-node list ------------------------------------------
-// A warp whose 32 nodes are all bulk (eight fluid neighbours, no periodic
-// image) takes a path with no flag load, no adhesion and no bounce-back; any
-// other warp takes the general one for all its nodes. All lanes of the warp
-// must call this (t >= nfluid marks an idle lane).
+// Three paths, chosen per warp so that a warp never splits between them: a
+// warp whose 32 nodes are all bulk (eight fluid neighbours, away from
+// periodic borders) loads no flags and has no adhesion and no bounce-back;
+// a warp with wall nodes but none near a periodic border stores bounced
+// slots at k - c_i; any other warp takes the general path with periodic
+// images. All lanes of the warp must call this (t >= nfluid marks an idle
+// lane).
 template <typename T>
 __device__ __forceinline__ void collide_node(const T* __restrict__ f, T* __restrict__ fo,
                                              const typename Pop<T>::C* __restrict__ P,
@@ -166,8 +227,13 @@ __device__ __forceinline__ void collide_node(const T* __restrict__ f, T* __restr
   const bool valid = t < nfluid;
   const unsigned e = valid ? (unsigned)__ldg(list + t) : 0u;
   const bool warp_edge = __any_sync(0xffffffffu, (e & EDGE_TAG) != 0u);
+  const bool warp_border = __any_sync(0xffffffffu, (e & BORDER_TAG) != 0u);
   if (!valid) return;
-  const int k = (int)(e & ~EDGE_TAG);
+  if constexpr (sizeof(C) == 4) {
+    collide_node_pair<T>(f, fo, P, Pref, flags, e, warp_edge, warp_border, g, ph);
+    return;
+  }
+  const int k = (int)(e & ~LIST_TAGS);
   const uint16_t fl = warp_edge ? __ldg(flags + k) : uint16_t(0);
   C ref[2][9];
   pull_refs<T>(Pref, g, k, fl, warp_edge, ref);
@@ -190,7 +256,7 @@ __device__ __forceinline__ void collide_node(const T* __restrict__ f, T* __restr
   const C uy = ((jyA + jyB) + C(0.5) * (F[0][1] + F[1][1])) * inv;
   collide(fv, rho, ux, uy, F, ph.omega, ph.kF);
   write_refs<T>(rho, ref);
-  if (!warp_edge) {
+  if (!warp_border) {
     T* p = fo + k;
 #pragma unroll
     for (int s = 0; s < 2; ++s)
@@ -199,6 +265,7 @@ __device__ __forceinline__ void collide_node(const T* __restrict__ f, T* __restr
         Pop<T>::st(p, 0, fv[s][i], ref[s][i]);
         p += g.plane;
       }
+    if (warp_edge) store_bounced_near(fo, g, k, fl, fv, ref);
   } else {
     int x, y;
     coords(g, k, x, y);

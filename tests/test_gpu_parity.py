@@ -194,6 +194,33 @@ def test_checkpoint_restore_is_exact():
     assert torch.equal(a.populations(), b.populations())
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp64"])
+@pytest.mark.parametrize("wet", ["mc", "llkc_self", "improved", "improved_self_d2q9", "constant"])
+@pytest.mark.parametrize("case", ["porous_periodic", "wall_walled"])
+def test_fused_matches_two_pass_bitwise(storage, wet, case):
+    """Both schedules run the same node arithmetic and the same density sums
+    in the same order, so they must agree bit for bit (several 30-column
+    strips of the single-pass kernel plus a ragged one, row segments)."""
+    if case == "porous_periodic":
+        nx, ny, per = 157, 131, (True, True)
+        mask = inputs.porous_disks(nx, ny, 0.35, rmin=3, rmax=9, seed=5)
+        rA, rB = inputs.pore_droplets(mask, 0.3, rmin=3, rmax=8, seed=6)
+    else:
+        nx, ny, per = 123, 77, (False, False)
+        mask = inputs.inclined_wall_mask(nx, ny, 20.0, 12)
+        rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, ny / 2, 12)
+    _, (kind, gkw) = WETTINGS[wet]
+    outs = []
+    for kernel in KERNELS:
+        s = lbm.Simulation(nx, ny, periodic_x=per[0], periodic_y=per[1], storage=storage, kernel=kernel)
+        s.set_geometry(mask).set_wetting(kind, **gkw).init_fields(rA, rB).step(37)
+        outs.append((s.populations(), s.moments(), s.mass()))
+    assert torch.equal(outs[0][0], outs[1][0])
+    for a, b in zip(outs[0][1], outs[1][1]):
+        assert torch.equal(a, b)
+    assert np.array_equal(outs[0][2], outs[1][2])
+
+
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_deterministic(kernel):
     nx, ny = 150, 64
