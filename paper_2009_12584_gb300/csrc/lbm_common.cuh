@@ -88,6 +88,15 @@ __device__ __forceinline__ void put_with_ghosts(V* plane, const Geo& g, int x, i
 // Population storage. FP32/FP64 store f itself. FP16/BF16 store the
 // deviation f - w_i rho_ref^sigma, which keeps the rest-state part exact and
 // spends the 11/8 significand bits on what varies.
+//
+// Layout: nine planes of component pairs. The populations of components A
+// and B for direction i at padded index k are adjacent, at element
+// pslot(g, i, k) + s, so that one vector access (8 bytes for FP32) moves
+// both and each plane streams as a single sequence.
+__host__ __device__ __forceinline__ int64_t pslot(const Geo& g, int i, int64_t k) {
+  return ((int64_t)i * g.plane + k) * 2;
+}
+
 template <typename T>
 struct Pop;
 template <>
@@ -97,6 +106,14 @@ struct Pop<float> {
   static __device__ __forceinline__ void st(float* p, int64_t k, float v, float) { p[k] = v; }
   static __device__ __forceinline__ float enc(float v, float) { return v; }
   static __device__ __forceinline__ float dec(float v, float) { return v; }
+  static __device__ __forceinline__ void ld2(const float* p, int64_t j, float, float, float& a, float& b) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p + j));
+    a = v.x;
+    b = v.y;
+  }
+  static __device__ __forceinline__ void st2(float* p, int64_t j, float a, float b, float, float) {
+    *reinterpret_cast<float2*>(p + j) = make_float2(a, b);
+  }
 };
 template <>
 struct Pop<double> {
@@ -105,6 +122,14 @@ struct Pop<double> {
   static __device__ __forceinline__ void st(double* p, int64_t k, double v, double) { p[k] = v; }
   static __device__ __forceinline__ double enc(double v, double) { return v; }
   static __device__ __forceinline__ double dec(double v, double) { return v; }
+  static __device__ __forceinline__ void ld2(const double* p, int64_t j, double, double, double& a, double& b) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p + j));
+    a = v.x;
+    b = v.y;
+  }
+  static __device__ __forceinline__ void st2(double* p, int64_t j, double a, double b, double, double) {
+    *reinterpret_cast<double2*>(p + j) = make_double2(a, b);
+  }
 };
 template <>
 struct Pop<__half> {
@@ -117,6 +142,14 @@ struct Pop<__half> {
   }
   static __device__ __forceinline__ __half enc(float v, float ref) { return __float2half_rn(v - ref); }
   static __device__ __forceinline__ float dec(__half v, float ref) { return __half2float(v) + ref; }
+  static __device__ __forceinline__ void ld2(const __half* p, int64_t j, float ra, float rb, float& a, float& b) {
+    const __half2 v = __ldg(reinterpret_cast<const __half2*>(p + j));
+    a = __low2float(v) + ra;
+    b = __high2float(v) + rb;
+  }
+  static __device__ __forceinline__ void st2(__half* p, int64_t j, float a, float b, float ra, float rb) {
+    *reinterpret_cast<__half2*>(p + j) = __floats2half2_rn(a - ra, b - rb);
+  }
 };
 template <>
 struct Pop<__nv_bfloat16> {
@@ -129,6 +162,15 @@ struct Pop<__nv_bfloat16> {
   }
   static __device__ __forceinline__ __nv_bfloat16 enc(float v, float ref) { return __float2bfloat16_rn(v - ref); }
   static __device__ __forceinline__ float dec(__nv_bfloat16 v, float ref) { return __bfloat162float(v) + ref; }
+  static __device__ __forceinline__ void ld2(const __nv_bfloat16* p, int64_t j, float ra, float rb, float& a,
+                                             float& b) {
+    const __nv_bfloat162 v = __ldg(reinterpret_cast<const __nv_bfloat162*>(p + j));
+    a = __low2float(v) + ra;
+    b = __high2float(v) + rb;
+  }
+  static __device__ __forceinline__ void st2(__nv_bfloat16* p, int64_t j, float a, float b, float ra, float rb) {
+    *reinterpret_cast<__nv_bfloat162*>(p + j) = __floats2bfloat162_rn(a - ra, b - rb);
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -345,13 +387,9 @@ __device__ __forceinline__ void store_bounced(T* __restrict__ fo, const Geo& g, 
     if (g.per_x) sx = (sx + g.nx) % g.nx;
     if (g.per_y) sy = (sy + g.ny) % g.ny;
     const int ks = g.idx(sx, sy);
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      T* plane = fo + (int64_t)(s * 9 + i) * g.plane;
-      const C v = fv[s][opp_of(i)], r = ref[s][i];
-      Pop<T>::st(plane, ks, v, r);
-      for_ghost_images(g, sx, sy, [&](int kk) { Pop<T>::st(plane, kk, v, r); });
-    }
+    const C a = fv[0][opp_of(i)], b = fv[1][opp_of(i)], ra = ref[0][i], rb = ref[1][i];
+    Pop<T>::st2(fo, pslot(g, i, ks), a, b, ra, rb);
+    for_ghost_images(g, sx, sy, [&](int kk) { Pop<T>::st2(fo, pslot(g, i, kk), a, b, ra, rb); });
   }
 }
 
@@ -365,9 +403,7 @@ __device__ __forceinline__ void store_bounced_near(T* __restrict__ fo, const Geo
   for (int i = 1; i < 9; ++i) {
     if (!(fl & nb_bit(opp_of(i)))) continue;
     const int ks = k - cx_of(i) - cy_of(i) * g.px;
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-      Pop<T>::st(fo + (int64_t)(s * 9 + i) * g.plane, ks, fv[s][opp_of(i)], ref[s][i]);
+    Pop<T>::st2(fo, pslot(g, i, ks), fv[0][opp_of(i)], fv[1][opp_of(i)], ref[0][i], ref[1][i]);
   }
 }
 
@@ -376,24 +412,15 @@ __device__ __forceinline__ void store_bounced_near(T* __restrict__ fo, const Geo
 template <typename T, typename C>
 __device__ __forceinline__ void store_node(T* __restrict__ fo, const Geo& g, int x, int y, int k,
                                            const C fv[2][9], const C ref[2][9]) {
-  T* p = fo + k;
 #pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      Pop<T>::st(p, 0, fv[s][i], ref[s][i]);
-      p += g.plane;
-    }
+  for (int i = 0; i < 9; ++i) Pop<T>::st2(fo, pslot(g, i, k), fv[0][i], fv[1][i], ref[0][i], ref[1][i]);
   const bool img = (g.per_x && (x < GH || x >= g.nx - GH)) || (g.per_y && (y < GH || y >= g.ny - GH));
   if (img) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        T* plane = fo + (int64_t)(s * 9 + i) * g.plane;
-        const C v = fv[s][i], r = ref[s][i];
-        for_ghost_images(g, x, y, [&](int kk) { Pop<T>::st(plane, kk, v, r); });
-      }
+    for (int i = 0; i < 9; ++i) {
+      const C a = fv[0][i], b = fv[1][i], ra = ref[0][i], rb = ref[1][i];
+      for_ghost_images(g, x, y, [&](int kk) { Pop<T>::st2(fo, pslot(g, i, kk), a, b, ra, rb); });
+    }
   }
 }
 

@@ -131,10 +131,8 @@ __global__ void __launch_bounds__(MARCH_WARPS * 32, 4)
     if (computable && !(fl & F_SOLID)) {
       const int k = g.idx(xc, y);
 #pragma unroll
-      for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-          fv[s][i] = Pop<T>::ld(f + (int64_t)(s * 9 + i) * PL, k - cx_of(i) - cy_of(i) * g.px, ref[s][i]);
+      for (int i = 0; i < 9; ++i)
+        Pop<T>::ld2(f, pslot(g, i, k - cx_of(i) - cy_of(i) * g.px), ref[0][i], ref[1][i], fv[0][i], fv[1][i]);
     }
   };
   load_row(y0 - 2, p0, o0);
@@ -188,14 +186,9 @@ __global__ void __launch_bounds__(MARCH_WARPS * 32, 4)
           store_node(fo, g, xc, y, k, fv, ref);
           store_bounced(fo, g, xc, y, fl, fv, ref);
         } else {
-          T* p = fo + k;
 #pragma unroll
-          for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-              Pop<T>::st(p, 0, fv[s][i], ref[s][i]);
-              p += PL;
-            }
+          for (int i = 0; i < 9; ++i)
+            Pop<T>::st2(fo, pslot(g, i, k), fv[0][i], fv[1][i], ref[0][i], ref[1][i]);
           if (fl & NB_ANY) store_bounced_near(fo, g, k, fl, fv, ref);
         }
       }

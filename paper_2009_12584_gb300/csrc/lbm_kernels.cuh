@@ -25,10 +25,8 @@ template <typename T, typename C = typename Pop<T>::C>
 __device__ __forceinline__ void gather(const T* __restrict__ f, const Geo& g, int k, const C ref[2][9],
                                        C out[2][9]) {
 #pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int i = 0; i < 9; ++i)
-      out[s][i] = Pop<T>::ld(f + (int64_t)(s * 9 + i) * g.plane, k - cx_of(i) - cy_of(i) * g.px, ref[s][i]);
+  for (int i = 0; i < 9; ++i)
+    Pop<T>::ld2(f, pslot(g, i, k - cx_of(i) - cy_of(i) * g.px), ref[0][i], ref[1][i], out[0][i], out[1][i]);
 }
 
 // Encoding references of 16-bit storage. A 2-byte population is stored as
@@ -165,9 +163,7 @@ __device__ __forceinline__ void collide_node_pair(const T* __restrict__ f, T* __
   float2 fp[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const int m = k - cx_of(i) - cy_of(i) * g.px;
-    fp[i] = f2(Pop<T>::ld(f + (int64_t)i * g.plane, m, ref[0][i]),
-               Pop<T>::ld(f + (int64_t)(9 + i) * g.plane, m, ref[1][i]));
+    Pop<T>::ld2(f, pslot(g, i, k - cx_of(i) - cy_of(i) * g.px), ref[0][i], ref[1][i], fp[i].x, fp[i].y);
   }
   float2 q[9];
   q[0] = f2(0.0f);
@@ -182,16 +178,14 @@ __device__ __forceinline__ void collide_node_pair(const T* __restrict__ f, T* __
   if (!warp_border) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      Pop<T>::st(fo + (int64_t)i * g.plane, k, fp[i].x, ref[0][i]);
-      Pop<T>::st(fo + (int64_t)(9 + i) * g.plane, k, fp[i].y, ref[1][i]);
+      Pop<T>::st2(fo, pslot(g, i, k), fp[i].x, fp[i].y, ref[0][i], ref[1][i]);
     }
     if (warp_edge) {
 #pragma unroll
       for (int i = 1; i < 9; ++i) {
         if (!(fl & nb_bit(opp_of(i)))) continue;
         const int ks = k - cx_of(i) - cy_of(i) * g.px;
-        Pop<T>::st(fo + (int64_t)i * g.plane, ks, fp[opp_of(i)].x, ref[0][i]);
-        Pop<T>::st(fo + (int64_t)(9 + i) * g.plane, ks, fp[opp_of(i)].y, ref[1][i]);
+        Pop<T>::st2(fo, pslot(g, i, ks), fp[opp_of(i)].x, fp[opp_of(i)].y, ref[0][i], ref[1][i]);
       }
     }
   } else {
@@ -257,14 +251,8 @@ __device__ __forceinline__ void collide_node(const T* __restrict__ f, T* __restr
   collide(fv, rho, ux, uy, F, ph.omega, ph.kF);
   write_refs<T>(rho, ref);
   if (!warp_border) {
-    T* p = fo + k;
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        Pop<T>::st(p, 0, fv[s][i], ref[s][i]);
-        p += g.plane;
-      }
+    for (int i = 0; i < 9; ++i) Pop<T>::st2(fo, pslot(g, i, k), fv[0][i], fv[1][i], ref[0][i], ref[1][i]);
     if (warp_edge) store_bounced_near(fo, g, k, fl, fv, ref);
   } else {
     int x, y;
@@ -275,7 +263,7 @@ __device__ __forceinline__ void collide_node(const T* __restrict__ f, T* __restr
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, 5) k_collide_list(const T* __restrict__ f, T* __restrict__ fo,
+__global__ void __launch_bounds__(256, 4) k_collide_list(const T* __restrict__ f, T* __restrict__ fo,
                                                          const typename Pop<T>::C* __restrict__ P,
                                                          const typename Pop<T>::C* __restrict__ Pref,
                                                          const uint16_t* __restrict__ flags,
@@ -527,11 +515,15 @@ __global__ void __launch_bounds__(256) k_mass_partial(const T* __restrict__ f,
     }
     C ref[2][9];
     write_refs<T>(rw, ref);
-    for (int s = 0; s < 2; ++s) {
-      double r = 0.0;
-      for (int i = 0; i < 9; ++i) r += (double)Pop<T>::ld(f + (int64_t)(s * 9 + i) * g.plane, k, ref[s][i]);
-      acc[s] += r;
+    double r[2] = {0.0, 0.0};
+    for (int i = 0; i < 9; ++i) {
+      C a, b;
+      Pop<T>::ld2(f, pslot(g, i, k), ref[0][i], ref[1][i], a, b);
+      r[0] += (double)a;
+      r[1] += (double)b;
     }
+    acc[0] += r[0];
+    acc[1] += r[1];
   }
   for (int s = 0; s < 2; ++s) {
     double v = acc[s];
