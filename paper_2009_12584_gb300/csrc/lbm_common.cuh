@@ -85,6 +85,41 @@ __device__ __forceinline__ void put_with_ghosts(V* plane, const Geo& g, int x, i
 }
 
 // ---------------------------------------------------------------------------
+// Density planes (rho, rho~ at interface-solid cells, and the encoding
+// references of 16-bit storage) hold (component A, component B) pairs: the
+// value of component s at padded index k is element 2 k + s.
+template <typename C>
+struct CPair;
+template <>
+struct CPair<float> {
+  using V = float2;
+};
+template <>
+struct CPair<double> {
+  using V = double2;
+};
+
+template <typename C>
+__device__ __forceinline__ void ldP(const C* __restrict__ P, int64_t k, C& a, C& b) {
+  const typename CPair<C>::V v = __ldg(reinterpret_cast<const typename CPair<C>::V*>(P) + k);
+  a = v.x;
+  b = v.y;
+}
+template <typename C>
+__device__ __forceinline__ void stP(C* __restrict__ P, int64_t k, C a, C b) {
+  typename CPair<C>::V v;
+  v.x = a;
+  v.y = b;
+  reinterpret_cast<typename CPair<C>::V*>(P)[k] = v;
+}
+// Store the pair at owned node (x, y) and at its periodic images.
+template <typename C>
+__device__ __forceinline__ void stP_ghosts(C* __restrict__ P, const Geo& g, int x, int y, C a, C b) {
+  stP(P, g.idx(x, y), a, b);
+  for_ghost_images(g, x, y, [&](int k) { stP(P, k, a, b); });
+}
+
+// ---------------------------------------------------------------------------
 // Population storage. FP32/FP64 store f itself. FP16/BF16 store the
 // deviation f - w_i rho_ref^sigma, which keeps the rest-state part exact and
 // spends the 11/8 significand bits on what varies.

@@ -101,7 +101,6 @@ __global__ void __launch_bounds__(MARCH_WARPS * 32, 4)
   const int xo = lane == 0 ? xc - 1 : xc + 1;  // the outer lanes' extra column
   const bool outer = (lane == 0 || lane == 31) && reads;
   const int y0 = blockIdx.y * H, y_end = min(g.ny, y0 + H);
-  const int64_t PL = g.plane;
   C ref[2][9];  // storage references: unused for 4- and 8-byte populations
 #pragma unroll
   for (int s = 0; s < 2; ++s)
@@ -117,13 +116,11 @@ __global__ void __launch_bounds__(MARCH_WARPS * 32, 4)
   auto load_row = [&](int y, C p[2], C o[2]) {
     if (reads) {
       const int k = g.idx(xc, y);
-      p[0] = __ldg(P + k);
-      p[1] = __ldg(P + PL + k);
+      ldP(P, k, p[0], p[1]);
     }
     if (outer) {
       const int k = g.idx(xo, y);
-      o[0] = __ldg(P + k);
-      o[1] = __ldg(P + PL + k);
+      ldP(P, k, o[0], o[1]);
     }
   };
   auto load_flags = [&](int y) -> uint16_t { return reads ? __ldg(flags + g.idx(xc, y)) : F_SOLID; };
@@ -213,8 +210,7 @@ __global__ void __launch_bounds__(MARCH_WARPS * 32, 4)
           const T raw = bounce ? b0[(s * 9 + o) * 32] : rb[(s * 9 + i) * 32 - cx_of(i)];
           fn[s][i] = Pop<T>::dec(raw, ref[s][i]);
         }
-      put_with_ghosts(Po, g, xc, r, density(fn[0]));
-      put_with_ghosts(Po + PL, g, xc, r, density(fn[1]));
+      stP_ghosts(Po, g, xc, r, density(fn[0]), density(fn[1]));
     }
     fl_prev = fl;
   }

@@ -46,13 +46,14 @@ __device__ __forceinline__ void pull_refs(const C* __restrict__ Pref, const Geo&
                                           C ref[2][9]) {
   if constexpr (kDev<T>) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const bool self = i == 0 || (check && (fl & nb_bit(opp_of(i))));
-        const int m = self ? k : k - cx_of(i) - cy_of(i) * g.px;
-        ref[s][i] = w_of<C>(i) * __ldg(Pref + s * g.plane + m);
-      }
+    for (int i = 0; i < 9; ++i) {
+      const bool self = i == 0 || (check && (fl & nb_bit(opp_of(i))));
+      const int m = self ? k : k - cx_of(i) - cy_of(i) * g.px;
+      C a, b;
+      ldP(Pref, m, a, b);
+      ref[0][i] = w_of<C>(i) * a;
+      ref[1][i] = w_of<C>(i) * b;
+    }
   } else {
 #pragma unroll
     for (int s = 0; s < 2; ++s)
@@ -87,19 +88,15 @@ __global__ void __launch_bounds__(128) k_density(const T* __restrict__ f, typena
   pull_refs<T>(Pref, g, k, fl, true, ref);
   C fv[2][9];
   gather<T>(f, g, k, ref, fv);
-  put_with_ghosts(P, g, x, y, density(fv[0]));
-  put_with_ghosts(P + g.plane, g, x, y, density(fv[1]));
+  stP_ghosts(P, g, x, y, density(fv[0]), density(fv[1]));
 }
 
 // Read the density plane at the 8 neighbours of padded index k.
 template <typename C>
 __device__ __forceinline__ void neighbour_P(const C* __restrict__ P, const Geo& g, int k, C nbP[2][9]) {
+  nbP[0][0] = nbP[1][0] = 0;
 #pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    nbP[s][0] = 0;
-#pragma unroll
-    for (int i = 1; i < 9; ++i) nbP[s][i] = __ldg(P + s * g.plane + k + cx_of(i) + cy_of(i) * g.px);
-  }
+  for (int i = 1; i < 9; ++i) ldP(P, k + cx_of(i) + cy_of(i) * g.px, nbP[0][i], nbP[1][i]);
 }
 
 // Owned coordinates of padded index k.
@@ -127,14 +124,12 @@ __device__ __forceinline__ void density_node(const T* __restrict__ f, typename P
   C fv[2][9];
   gather<T>(f, g, k, ref, fv);
   const C r0 = density(fv[0]), r1 = density(fv[1]);
-  P[k] = r0;
-  P[g.plane + k] = r1;
+  stP(P, k, r0, r1);
   if (e & BORDER_TAG) {  // may have periodic images
     int x, y;
     coords(g, k, x, y);
     for_ghost_images(g, x, y, [&](int kk) {
-      P[kk] = r0;
-      P[g.plane + kk] = r1;
+      stP(P, kk, r0, r1);
     });
   }
 }
@@ -170,7 +165,7 @@ __device__ __forceinline__ void collide_node_pair(const T* __restrict__ f, T* __
 #pragma unroll
   for (int i = 1; i < 9; ++i) {
     const int m = k + cx_of(i) + cy_of(i) * g.px;
-    q[i] = f2(__ldg(P + m), __ldg(P + g.plane + m));
+    q[i] = __ldg(reinterpret_cast<const float2*>(P) + m);
   }
   const float2 rho = warp_edge ? update_pair<true>(fp, q, fl, ph) : update_pair<false>(fp, q, fl, ph);
   const float rr[2] = {rho.x, rho.y};
@@ -290,8 +285,7 @@ __device__ __forceinline__ void virtual_density(const C* __restrict__ P, const u
       const int j = (dy + REACH) * (2 * REACH + 1) + (dx + REACH);
       const int m = k + dx + dy * g.px;
       fl[j] = __ldg(flags + m);
-      p0[j] = __ldg(P + m);
-      p1[j] = __ldg(P + g.plane + m);
+      ldP(P, m, p0[j], p1[j]);
     }
   C num0 = 0, num1 = 0, den = 0;
 #pragma unroll
@@ -328,8 +322,7 @@ __device__ __forceinline__ void virtual_density_node(C* __restrict__ P, const ui
     virtual_density<C, false>(P, flags, g, k, ph, v0, v1);
   int x, y;
   coords(g, k, x, y);
-  put_with_ghosts(P, g, x, y, v0);
-  put_with_ghosts(P + g.plane, g, x, y, v1);
+  stP_ghosts(P, g, x, y, v0, v1);
 }
 
 template <typename C>
@@ -468,8 +461,8 @@ __global__ void k_set_state(T* __restrict__ f, typename Pop<T>::C* __restrict__ 
     double r = 0.0;
     for (int j = 0; j < 9; ++j) r += O(n, s, j);
     rho0[s] = C(r);
-    put_with_ghosts(Pref + s * g.plane, g, x, y, rho0[s]);
   }
+  stP_ghosts(Pref, g, x, y, rho0[0], rho0[1]);
   C ref[2][9];
   write_refs<T>(rho0, ref);
   C fv[2][9];
@@ -510,8 +503,7 @@ __global__ void __launch_bounds__(256) k_mass_partial(const T* __restrict__ f,
     // a node's own slots were written by the node itself
     C rw[2] = {C(0), C(0)};
     if (kDev<T>) {
-      rw[0] = Pref[k];
-      rw[1] = Pref[g.plane + k];
+      ldP(Pref, k, rw[0], rw[1]);
     }
     C ref[2][9];
     write_refs<T>(rw, ref);
