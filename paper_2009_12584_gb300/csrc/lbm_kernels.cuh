@@ -13,13 +13,6 @@
 
 namespace lbm {
 
-struct Planes {
-  const void* f_in;   // 18 planes of the storage type
-  void* f_out;
-  void* P;            // 2 planes of the compute type: rho (fluid), rho~ (solid)
-  const uint16_t* flags;
-};
-
 // Pull the post-streaming populations of both components at padded index k.
 template <typename T, typename C = typename Pop<T>::C>
 __device__ __forceinline__ void gather(const T* __restrict__ f, const Geo& g, int k, const C ref[2][9],
@@ -447,20 +440,23 @@ __global__ void k_set_state(T* __restrict__ f, typename Pop<T>::C* __restrict__ 
   if (fl & F_SOLID) return;
   const int64_t N = (int64_t)g.nx * g.ny;
   // O at node m, component s, direction j
-  auto O = [&](int64_t m, int s, int j) -> double {
-    if (SRC == 0) return fin[(s * 9 + j) * N + m];
-    const double r = s ? rB[m] : rA[m];
-    const double vx = ux ? ux[m] : 0.0, vy = uy ? uy[m] : 0.0;
-    const double cu = cx_of(j) * vx + cy_of(j) * vy;
-    return r * w_of<double>(j) * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (vx * vx + vy * vy));
+  // evaluated in the compute type: FP32 for 4- and 2-byte storage (FP64
+  // arithmetic is a small fraction of the FP32 rate on this GPU), FP64 for
+  // FP64 storage
+  auto O = [&](int64_t m, int s, int j) -> C {
+    if (SRC == 0) return C(fin[(s * 9 + j) * N + m]);
+    const C r = C(s ? rB[m] : rA[m]);
+    const C vx = ux ? C(ux[m]) : C(0), vy = uy ? C(uy[m]) : C(0);
+    const C cu = C(cx_of(j)) * vx + C(cy_of(j)) * vy;
+    return r * w_of<C>(j) * (C(1) + C(3) * cu + C(4.5) * cu * cu - C(1.5) * (vx * vx + vy * vy));
   };
   const int64_t n = (int64_t)y * g.nx + x;
   C rho0[2];
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
-    double r = 0.0;
+    C r = C(0);
     for (int j = 0; j < 9; ++j) r += O(n, s, j);
-    rho0[s] = C(r);
+    rho0[s] = r;
   }
   stP_ghosts(Pref, g, x, y, rho0[0], rho0[1]);
   C ref[2][9];
