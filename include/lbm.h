@@ -194,6 +194,56 @@ lbm_status lbm_set_populations(lbm_ctx* ctx, const double* d_f);
  * writes h_out[2] on the host. */
 lbm_status lbm_mass(lbm_ctx* ctx, double* h_out);
 
+/* ---- On-device diagnostics ----------------------------------------------
+ * The measurements of Secs. 3-4 of arXiv:2009.12584, reduced on the device
+ * from the current moments (rho^A, u of Eq. 3) so that long runs copy no
+ * fields to the host:
+ *  - sliding velocity (Sec. 3.1): centre-of-mass velocity of the A phase
+ *    weighted by w = max(rho^A - rho_out, 0) at fluid nodes, and its
+ *    projection on a unit tangent;
+ *  - contact angle (Sec. 3.2): the points where rho^A crosses `level` on grid
+ *    edges joining two fluid nodes (linear interpolation), minus those within
+ *    `exclude` of the wall line (and outside `box`), fitted by the algebraic
+ *    least-squares (Kasa) circle; cos(theta) = -h / R with h the signed
+ *    distance from the wall line to the centre, positive on the fluid side
+ *    (the left-hand normal of the wall direction (cos b, sin b));
+ *  - bridge radius (Sec. 4): on column bridge_x, the distance from the
+ *    halfway wall (half a node below bridge_y0, the first fluid node above
+ *    the surface) to the first point above it where rho^A drops through
+ *    `level`; 0 while rho^A(bridge_x, bridge_y0) < level;
+ *  - max |u| over fluid nodes (the spurious-current level of Sec. 4).
+ * Sums are FP64 in a fixed order (deterministic); the 3x3 normal equations of
+ * the fit are solved on the host. Contour edges do not wrap periodic axes. */
+typedef struct {
+  double level;           /* rho^A level of the interface, e.g. 0.5 */
+  double rho_out;         /* weight offset: w = max(rho^A - rho_out, 0) */
+  double tangent[2];      /* unit direction of the sliding velocity */
+  double wall_point[2];   /* a point of the wall line (lattice units) */
+  double wall_angle_deg;  /* direction of the wall line, degrees from +x */
+  double exclude;         /* contour points closer than this to the wall are dropped */
+  double box[4];          /* x0, x1, y0, y1: points outside are dropped; x1 < x0: no box */
+  int32_t bridge_x;       /* column of the bridge radius; -1: not measured */
+  int32_t bridge_y0;      /* first fluid node above the surface on that column */
+} lbm_diag_params;
+
+typedef struct {
+  double weight;           /* sum of w */
+  double com[2];           /* centre of mass of w (NaN if the weight is 0) */
+  double com_velocity[2];  /* w-weighted mean of u */
+  double sliding_velocity; /* com_velocity . tangent */
+  double max_u;            /* max |u| over fluid nodes */
+  int64_t contour_points;  /* crossings kept for the fit */
+  double circle[3];        /* xc, yc, R of the fit (NaN with fewer than 3 points) */
+  double contact_angle_deg;/* through the A phase (NaN without a circle) */
+  double bridge_radius;    /* 0 if not measured */
+} lbm_diag;
+
+/* Fill *h_out (host) for the current state. Uses the workspace's staging
+ * area (as lbm_moments does) and synchronises. LBM_ERR_ARG for a null
+ * pointer, level outside (0, 2), a non-finite parameter or a bridge column
+ * or row outside the grid; LBM_ERR_STATE before geometry and fields. */
+lbm_status lbm_diagnostics(lbm_ctx* ctx, const lbm_diag_params* params, lbm_diag* h_out);
+
 /* Number of interface-solid nodes of the installed geometry. */
 lbm_status lbm_interface_count(lbm_ctx* ctx, int64_t* n);
 

@@ -6,6 +6,7 @@
 
 #include <new>
 
+#include "lbm_diag.cuh"
 #include "lbm_internal.cuh"
 
 using namespace lbm;
@@ -38,7 +39,7 @@ bool make_geo(const lbm_params* p, Geo* g) {
 }
 
 struct Layout {
-  size_t f, P, flags, list, flist, counts, small, partial, mass, smask, stage, total;
+  size_t f, P, flags, list, flist, counts, small, partial, mass, smask, stage, dpart, total;
 };
 
 constexpr int MASS_BLOCKS = 1024;
@@ -62,6 +63,7 @@ bool layout(const lbm_params* p, const Geo& g, Layout* L) {
   L->mass = off;     off = align_up(off + 16, A);
   L->smask = off;    off = align_up(off + (size_t)N, A);
   L->stage = off;    off = align_up(off + 4 * (size_t)N * 8, A);
+  L->dpart = off;    off = align_up(off + ((size_t)DIAG_BLOCKS * DIAG_NRED + DIAG_NQ) * 8, A);
   L->total = off;
   return true;
 }
@@ -329,6 +331,7 @@ lbm_status lbm_create(const lbm_params* params, void* d_workspace, size_t bytes,
   c->mass_out = (double*)(c->ws + L.mass);
   c->stage_mask = (uint8_t*)(c->ws + L.smask);
   c->stage = (double*)(c->ws + L.stage);
+  c->dpart = (double*)(c->ws + L.dpart);
   const int64_t N = (int64_t)params->nx * params->ny;
   c->if_capacity = params->max_interface > 0 ? params->max_interface : N;
   c->scan_blocks = (int)((N + SCAN_BLOCK - 1) / SCAN_BLOCK);
@@ -543,6 +546,103 @@ lbm_status lbm_mass(lbm_ctx* c, double* h_out) {
   s = check_cuda(c, cudaMemcpyAsync(h_out, c->mass_out, 16, cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
   if (!s) s = check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   return s;
+}
+
+lbm_status lbm_diagnostics(lbm_ctx* c, const lbm_diag_params* p, lbm_diag* h_out) {
+  if (!c || !p || !h_out) return LBM_ERR_ARG;
+  if (!c->has_geometry || !c->has_fields) return fail(c, LBM_ERR_STATE, "lbm_diagnostics before geometry and fields");
+  const double vals[] = {p->level, p->rho_out, p->tangent[0], p->tangent[1], p->wall_point[0], p->wall_point[1],
+                         p->wall_angle_deg, p->exclude, p->box[0], p->box[1], p->box[2], p->box[3]};
+  for (double v : vals)
+    if (!isfinite(v)) return fail(c, LBM_ERR_ARG, "lbm_diagnostics: non-finite parameter");
+  if (!(p->level > 0.0 && p->level < 2.0)) return fail(c, LBM_ERR_ARG, "lbm_diagnostics: level outside (0, 2)");
+  if (p->bridge_x >= 0 && (p->bridge_x >= c->g.nx || p->bridge_y0 < 0 || p->bridge_y0 >= c->g.ny))
+    return fail(c, LBM_ERR_ARG, "lbm_diagnostics: bridge column or row outside the grid");
+  DiagArgs a;
+  a.level = p->level;
+  a.rho_out = p->rho_out;
+  a.wx = p->wall_point[0];
+  a.wy = p->wall_point[1];
+  const double b = p->wall_angle_deg * (M_PI / 180.0);
+  a.nx_ = -sin(b);
+  a.ny_ = cos(b);
+  a.exclude = p->exclude;
+  for (int i = 0; i < 4; ++i) a.box[i] = p->box[i];
+  a.use_box = p->box[1] >= p->box[0];
+  a.ox = 0.5 * c->g.nx;  // the fit is translation invariant; centring keeps its sums well scaled
+  a.oy = 0.5 * c->g.ny;
+  a.bridge_x = p->bridge_x;
+  a.bridge_y0 = p->bridge_y0;
+  lbm_status s;
+  LBM_DISPATCH(c, s = (do_eval<T, 1>(c, c->stage)); break);
+  if (s) return s;
+  double* out_d = c->dpart + (size_t)DIAG_BLOCKS * DIAG_NRED;
+  k_diag_partial<<<DIAG_BLOCKS, DIAG_THREADS, 0, c->stream>>>(c->stage, c->flags, c->g, a, c->dpart);
+  if ((s = after_launch(c, "k_diag_partial"))) return s;
+  k_diag_final<<<1, 32, 0, c->stream>>>(c->dpart, c->stage, c->g, a, out_d);
+  if ((s = after_launch(c, "k_diag_final"))) return s;
+  double q[DIAG_NQ];
+  s = check_cuda(c, cudaMemcpyAsync(q, out_d, sizeof(q), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+  if (!s) s = check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (s) return s;
+  const double nan = NAN;
+  lbm_diag& o = *h_out;
+  o.weight = q[0];
+  o.com[0] = q[0] > 0 ? q[1] / q[0] : nan;
+  o.com[1] = q[0] > 0 ? q[2] / q[0] : nan;
+  o.com_velocity[0] = q[0] > 0 ? q[3] / q[0] : nan;
+  o.com_velocity[1] = q[0] > 0 ? q[4] / q[0] : nan;
+  o.sliding_velocity = o.com_velocity[0] * p->tangent[0] + o.com_velocity[1] * p->tangent[1];
+  o.max_u = sqrt(q[14]);
+  o.contour_points = (int64_t)q[5];
+  o.circle[0] = o.circle[1] = o.circle[2] = nan;
+  o.contact_angle_deg = nan;
+  o.bridge_radius = q[15];
+  if (q[5] >= 3) {
+    // normal equations of min sum (x^2 + y^2 - A x - B y - C)^2 (Kasa fit),
+    // solved by Gaussian elimination with partial pivoting
+    double M[3][4] = {{q[8], q[10], q[6], q[11]}, {q[10], q[9], q[7], q[12]}, {q[6], q[7], q[5], q[13]}};
+    bool ok = true;
+    for (int col = 0; col < 3 && ok; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < 3; ++r)
+        if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+      if (!(fabs(M[piv][col]) > 0)) {
+        ok = false;
+        break;
+      }
+      if (piv != col)
+        for (int j = 0; j < 4; ++j) {
+          const double t = M[col][j];
+          M[col][j] = M[piv][j];
+          M[piv][j] = t;
+        }
+      for (int r = col + 1; r < 3; ++r) {
+        const double fct = M[r][col] / M[col][col];
+        for (int j = col; j < 4; ++j) M[r][j] -= fct * M[col][j];
+      }
+    }
+    if (ok) {
+      double sol[3];
+      for (int r = 2; r >= 0; --r) {
+        double v = M[r][3];
+        for (int j = r + 1; j < 3; ++j) v -= M[r][j] * sol[j];
+        sol[r] = v / M[r][r];
+      }
+      const double xc = 0.5 * sol[0], yc = 0.5 * sol[1];
+      const double R2 = sol[2] + xc * xc + yc * yc;
+      if (R2 > 0) {
+        const double R = sqrt(R2);
+        o.circle[0] = xc + a.ox;
+        o.circle[1] = yc + a.oy;
+        o.circle[2] = R;
+        const double h = (o.circle[0] - a.wx) * a.nx_ + (o.circle[1] - a.wy) * a.ny_;
+        const double cth = fmax(-1.0, fmin(1.0, -h / R));
+        o.contact_angle_deg = acos(cth) * (180.0 / M_PI);
+      }
+    }
+  }
+  return LBM_OK;
 }
 
 lbm_status lbm_interface_count(lbm_ctx* c, int64_t* n) {

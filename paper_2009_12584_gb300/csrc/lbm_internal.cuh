@@ -36,6 +36,7 @@ struct lbm_ctx {
   double* mass_out;    // 2 doubles
   uint8_t* stage_mask; // lbm_run_host staging
   double* stage;       // 4 arrays of nx*ny doubles
+  double* dpart;       // diagnostics: per-block partial sums, then the reduced values
   int64_t if_capacity;
   int scan_blocks;
   int mass_blocks;

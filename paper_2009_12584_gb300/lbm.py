@@ -43,10 +43,29 @@ class LbmWetting(ctypes.Structure):
     ]
 
 
+class LbmDiagParams(ctypes.Structure):
+    _fields_ = [
+        ("level", ctypes.c_double), ("rho_out", ctypes.c_double),
+        ("tangent", ctypes.c_double * 2), ("wall_point", ctypes.c_double * 2),
+        ("wall_angle_deg", ctypes.c_double), ("exclude", ctypes.c_double),
+        ("box", ctypes.c_double * 4), ("bridge_x", ctypes.c_int32), ("bridge_y0", ctypes.c_int32),
+    ]
+
+
+class LbmDiag(ctypes.Structure):
+    _fields_ = [
+        ("weight", ctypes.c_double), ("com", ctypes.c_double * 2),
+        ("com_velocity", ctypes.c_double * 2), ("sliding_velocity", ctypes.c_double),
+        ("max_u", ctypes.c_double), ("contour_points", ctypes.c_int64),
+        ("circle", ctypes.c_double * 3), ("contact_angle_deg", ctypes.c_double),
+        ("bridge_radius", ctypes.c_double),
+    ]
+
+
 EXPORTS = [
     "lbm_workspace_bytes", "lbm_create", "lbm_set_stream", "lbm_set_geometry", "lbm_set_wetting",
     "lbm_init_fields", "lbm_step", "lbm_step_profiled", "lbm_moments", "lbm_forces", "lbm_get_populations",
-    "lbm_set_populations", "lbm_mass", "lbm_interface_count", "lbm_sync", "lbm_run_host",
+    "lbm_set_populations", "lbm_mass", "lbm_diagnostics", "lbm_interface_count", "lbm_sync", "lbm_run_host",
     "lbm_destroy", "lbm_status_str", "lbm_last_error", "lbm_launch_count",
     "lbm_batch_workspace_bytes", "lbm_batch_create", "lbm_batch_set_graph_steps", "lbm_batch_step",
     "lbm_batch_autotune", "lbm_batch_launch_count", "lbm_batch_last_error", "lbm_batch_destroy",
@@ -96,6 +115,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "lbm_get_populations": [vp, dp],
             "lbm_set_populations": [vp, dp],
             "lbm_mass": [vp, ctypes.POINTER(ctypes.c_double)],
+            "lbm_diagnostics": [vp, ctypes.POINTER(LbmDiagParams), ctypes.POINTER(LbmDiag)],
             "lbm_interface_count": [vp, ctypes.POINTER(i64)],
             "lbm_sync": [vp],
             "lbm_run_host": [vp, W, vp, vp, vp, i32, vp, vp, vp, vp],
@@ -259,6 +279,34 @@ class Simulation:
         out = (ctypes.c_double * 2)()
         self._check(self.lib.lbm_mass(self.h, out), "lbm_mass")
         return np.array([out[0], out[1]])
+
+    def diagnostics(self, *, level=0.5, rho_out=0.055, tangent=(1.0, 0.0), wall_point=(0.0, 0.5),
+                    wall_angle_deg=0.0, exclude=3.0, box=None, bridge=None) -> dict:
+        """Device-side measurements of the current state (lbm_diagnostics):
+        weighted centre of mass and its velocity, sliding velocity along
+        ``tangent``, max |u|, circle fit of the rho^A = ``level`` contour and
+        the contact angle on the wall line through ``wall_point`` at
+        ``wall_angle_deg``, and the bridge radius on column ``bridge[0]``
+        above the first fluid row ``bridge[1]``. ``box`` = (x0, x1, y0, y1)
+        keeps only contour points inside it."""
+        p = LbmDiagParams()
+        p.level, p.rho_out = level, rho_out
+        p.tangent[0], p.tangent[1] = tangent
+        p.wall_point[0], p.wall_point[1] = wall_point
+        p.wall_angle_deg, p.exclude = wall_angle_deg, exclude
+        b = box if box is not None else (1.0, 0.0, 0.0, 0.0)
+        for i in range(4):
+            p.box[i] = b[i]
+        p.bridge_x, p.bridge_y0 = bridge if bridge is not None else (-1, 0)
+        o = LbmDiag()
+        self._check(self.lib.lbm_diagnostics(self.h, ctypes.byref(p), ctypes.byref(o)), "lbm_diagnostics")
+        return {
+            "weight": o.weight, "com": (o.com[0], o.com[1]),
+            "com_velocity": (o.com_velocity[0], o.com_velocity[1]),
+            "sliding_velocity": o.sliding_velocity, "max_u": o.max_u,
+            "contour_points": o.contour_points, "circle": (o.circle[0], o.circle[1], o.circle[2]),
+            "contact_angle_deg": o.contact_angle_deg, "bridge_radius": o.bridge_radius,
+        }
 
     def interface_count(self):
         n = ctypes.c_int64()

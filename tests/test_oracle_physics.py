@@ -17,7 +17,8 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_2009_12584_gb300 import diag, inputs
+from oracle import diag
+from paper_2009_12584_gb300 import inputs
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_physics.txt")
 
@@ -78,7 +79,7 @@ def _slide(bc_kw, steps=3000):
     o = oracle.Oracle(nx, ny, mask, **bc_kw).init(rA, rB).step(steps)
     rho, _, _, u = o.fields()
     t = (math.cos(math.radians(beta)), math.sin(math.radians(beta)))
-    return diag.com_velocity(rho[0], u, 0.06, t)
+    return diag.sliding_velocity(rho[0], u, mask, 0.06, t)
 
 
 @pytest.mark.parametrize("kw", [dict(bc=oracle.BC_MARTYS_CHEN, G_s=(-0.2, 0.2)),
@@ -100,7 +101,7 @@ def _angle(kw, steps=3000):
     rA, rB = rA * (1 - mask), rB * (1 - mask)
     o = oracle.Oracle(nx, ny, mask, periodic_x=True, **kw).init(rA, rB).step(steps)
     rho, _, _, _ = o.fields()
-    return diag.contact_angle(rho[0], mask, (0, 0.5), 0.0)
+    return diag.contact_angle(rho[0], mask, (0, 0.5), 0.0)[0]
 
 
 def test_wetting_direction_martys_chen():
