@@ -1,0 +1,223 @@
+"""Paper-scale experiments of arXiv:2009.12584 run through the library, with
+every measurement taken on the device (``Simulation.diagnostics``):
+
+- ``contact_angle_sweep`` (Sec. 3.2): a droplet on a plane inclined at beta
+  under the improved virtual-density scheme, 1000 x 1000, tau = 1.88,
+  R0 = 100; the equilibrium contact angle as a function of xi and beta (the
+  paper reports the droplet at rest for every beta and theta = 71 degrees at
+  xi = -0.2, quoted in Sec. 4). All runs of the sweep advance together as
+  one batch.
+- ``coalescence`` (Sec. 4): two droplets with contact angle theta_c on a
+  flat (or circular) surface, smoothed initial interfaces, box 14 R0 x 10 R0;
+  the bridge radius b(t) on the symmetry column, in the reduced units of the
+  paper (t / tau_nu with tau_nu = eta R0 / sigma, b / R0), and the slope of
+  log b against log t in the viscous regime.
+- ``convergence``: ``coalescence`` on a flat surface at fixed Ohnesorge
+  number Oh = nu / sqrt(sigma R0) = 0.286 for R0 = 12.5 ... 400 (175 x 125 up
+  to 5600 x 4000), whose viscous slope the paper shows approaching the 2-D
+  prediction 0.857.
+
+Readings (shared with the rest of the library): xi maps to
+chi = (1 - xi, 1 + xi) with Eq. 7 as printed; sigma = 0.026 is the value
+the paper uses for Oh and tau_nu; nu = (tau - 1/2) / 3; the viscous window
+of the slope fit is b / R0 in [0.05, 1/3] after the early minimum of b
+(the paper puts the crossover at b ~ R0 / 3).
+
+    python -m paper_2009_12584_gb300.experiments sweep [--n 1000 --steps 200000]
+    python -m paper_2009_12584_gb300.experiments convergence [--radii 12.5 25 50 100 200 400]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import sys
+import time
+
+import numpy as np
+
+from . import inputs, lbm
+
+SIGMA = 0.026       # surface tension the paper uses at G_AB = 3 (Sec. 4)
+OH = 0.286          # Ohnesorge number of the convergence study (Sec. 4)
+THETA_C = 71.0      # contact angle of the coalescence runs, xi = -0.2 (Sec. 4)
+XI_C = -0.2
+
+
+def chi_from_xi(xi: float):
+    """chi^A, chi^B of Eq. 8 for the paper's xi (xi < 0 hydrophilic)."""
+    return (1.0 - xi, 1.0 + xi)
+
+
+def tau_from_nu(nu: float) -> float:
+    return 3.0 * nu + 0.5
+
+
+def wall_line(n: int, beta_deg: float, R0: float):
+    """A point of the staircase plane of Sec. 3.1 and its direction: the line
+    y = tan(beta) (x - L/2 - R0 sin(beta)) + L/2 - R0 cos(beta), tangent to
+    the initial droplet. On a flat wall (beta = 0) the point is moved to the
+    halfway plane above the last solid row."""
+    b = math.radians(beta_deg)
+    x0, y0 = n / 2 + R0 * math.sin(b), n / 2 - R0 * math.cos(b)
+    if beta_deg == 0.0:
+        y0 = math.ceil(y0) - 0.5
+    return (x0, y0), beta_deg
+
+
+def contact_angle_sweep(xis=(-0.4, -0.2, 0.0, 0.2, 0.4), betas=(0.0, 10.0, 20.0, 30.0, 45.0), *, n=1000,
+                        R0=100.0, tau=1.88, steps=200000, check_every=50000, avg_stencil=25, storage="fp32"):
+    """Equilibrium contact angle (and sliding velocity, max |u|) of a
+    droplet on the inclined plane for every (xi, beta), improved scheme.
+    Returns the parameters and one record per run with every check."""
+    runs = []
+    for beta in betas:
+        mask = inputs.inclined_wall_mask(n, n, beta, R0)
+        rA, rB = inputs.sharp_droplet(n, n, n / 2, n / 2, R0)
+        for xi in xis:
+            sim = lbm.Simulation(n, n, tau=(tau, tau), storage=storage)
+            sim.set_geometry(mask).set_wetting("virtual_avg", G_s=(3.0, 3.0), chi=chi_from_xi(xi),
+                                               avg_stencil=avg_stencil)
+            sim.init_fields(rA, rB)
+            runs.append({"xi": xi, "beta": beta, "sim": sim, "checks": []})
+    batch = lbm.Batch([r["sim"] for r in runs])
+    done, t0 = 0, time.time()
+    while done < steps:
+        k = min(check_every, steps - done)
+        batch.step(k)
+        done += k
+        for r in runs:
+            wp, ang = wall_line(n, r["beta"], R0)
+            b = math.radians(r["beta"])
+            d = r["sim"].diagnostics(level=0.5, rho_out=0.055, tangent=(math.cos(b), math.sin(b)),
+                                     wall_point=wp, wall_angle_deg=ang, exclude=3.0)
+            r["checks"].append({"step": done, "theta_deg": d["contact_angle_deg"],
+                                "sliding_velocity": d["sliding_velocity"], "max_u": d["max_u"],
+                                "contour_points": d["contour_points"]})
+    wall = time.time() - t0
+    batch.close()
+    out = []
+    for r in runs:
+        r["sim"].close()
+        out.append({"xi": r["xi"], "beta": r["beta"], "checks": r["checks"]})
+    return {"n": n, "R0": R0, "tau": tau, "steps": steps, "avg_stencil": avg_stencil, "storage": storage,
+            "wall_s": wall, "runs": out}
+
+
+def coalescence_setup(R0: float, *, Rs=None, theta_c=THETA_C, Oh=OH, sigma=SIGMA, delta=8.0):
+    """Grid, mask, initial densities and parameters of the Sec. 4 runs: box
+    14 R0 x 10 R0; surface (x - L_X/2)^2 + (y - (L_Y/2 - Rs))^2 = Rs^2, or
+    the half plane y < L_Y/2 for Rs = None; droplets centred at
+    x = L_X/2 -+ (R0 sin(theta_c) + 1), y = L_Y/2 - R0 cos(theta_c) with the
+    printed tanh profile; nu = Oh sqrt(sigma R0)."""
+    nx, ny = int(round(14 * R0)), int(round(10 * R0))
+    if Rs is None:
+        mask = inputs.flat_wall_mask(nx, ny, rows=ny // 2)
+    else:
+        mask = inputs.circle_surface_mask(nx, ny, nx / 2, ny / 2 - Rs, Rs, periodic=True)
+        mask[-1, :] = 1
+        mask[0, :] = 1
+    th = math.radians(theta_c)
+    dx = R0 * math.sin(th) + 1.0
+    rA, rB = inputs.tanh_droplets(nx, ny, (nx / 2 - dx, nx / 2 + dx), ny / 2 - R0 * math.cos(th), R0,
+                                  1.0, 0.055, delta)
+    rA, rB = rA * (1 - mask), rB * (1 - mask)
+    nu = Oh * math.sqrt(sigma * R0)
+    xb = nx // 2
+    col = mask[:, xb]
+    # first fluid node above the surface, whose top is at y = L_Y / 2
+    y0 = next(y for y in range(max(1, ny // 2 - 2), ny - 1) if col[y] == 0 and col[y - 1] == 1)
+    return {"nx": nx, "ny": ny, "mask": mask, "rhoA": rA, "rhoB": rB, "nu": nu, "tau": tau_from_nu(nu),
+            "tau_visc": nu * R0 / sigma, "bridge": (xb, y0)}
+
+
+def viscous_slope(t, b, R0, tau_visc, window=(0.05, 1.0 / 3.0)):
+    """Least-squares slope of log(b/R0) against log(t/tau_visc) over the
+    samples with b/R0 inside ``window`` that come after the smallest b seen
+    before the window's upper end (smoothed initial interfaces that already
+    overlap first relax); None with fewer than 3 samples."""
+    t, b = np.asarray(t, float), np.asarray(b, float)
+    inside = np.nonzero(b / R0 <= window[1])[0]
+    if len(inside) == 0:
+        return None
+    i0 = int(np.argmin(b[: inside[-1] + 1]))
+    sel = (b / R0 >= window[0]) & (b / R0 <= window[1]) & (t > 0) & (np.arange(len(t)) >= i0)
+    if sel.sum() < 3:
+        return None
+    return float(np.polyfit(np.log(t[sel] / tau_visc), np.log(b[sel] / R0), 1)[0])
+
+
+def coalescence(R0: float, *, Rs=None, t_end=1.0, samples=200, storage="fp32", xi=XI_C, theta_c=THETA_C):
+    """b(t) of two coalescing droplets up to t_end viscous times."""
+    s = coalescence_setup(R0, Rs=Rs, theta_c=theta_c)
+    sim = lbm.Simulation(s["nx"], s["ny"], tau=(s["tau"], s["tau"]), periodic_x=True, storage=storage)
+    sim.set_geometry(s["mask"]).set_wetting("virtual_avg", G_s=(3.0, 3.0), chi=chi_from_xi(xi))
+    sim.init_fields(s["rhoA"], s["rhoB"])
+    total = max(1, int(round(t_end * s["tau_visc"])))
+    every = max(1, total // samples)
+    ts, bs, us = [], [], []
+    t0 = time.time()
+    done = 0
+    while done < total:
+        k = min(every, total - done)
+        sim.step(k)
+        done += k
+        d = sim.diagnostics(bridge=s["bridge"], wall_point=(0.0, s["bridge"][1] - 0.5))
+        ts.append(done)
+        bs.append(d["bridge_radius"])
+        us.append(d["max_u"])
+    wall = time.time() - t0
+    sim.close()
+    return {"R0": R0, "Rs": Rs, "nx": s["nx"], "ny": s["ny"], "nu": s["nu"], "tau": s["tau"],
+            "tau_visc": s["tau_visc"], "steps": total, "wall_s": wall, "t": ts, "b": bs, "max_u": us,
+            "slope": viscous_slope(ts, bs, R0, s["tau_visc"])}
+
+
+def convergence(radii=(12.5, 25.0, 50.0, 100.0, 200.0, 400.0), *, t_end=1.0, storage="fp32"):
+    return [coalescence(R0, t_end=t_end, storage=storage) for R0 in radii]
+
+
+def _summary_sweep(res):
+    rows = []
+    for r in res["runs"]:
+        last = r["checks"][-1]
+        rows.append({"xi": r["xi"], "beta": r["beta"], "theta_deg": round(last["theta_deg"], 2),
+                     "theta_prev_deg": round(r["checks"][-2]["theta_deg"], 2) if len(r["checks"]) > 1 else None,
+                     "sliding_velocity": last["sliding_velocity"], "max_u": last["max_u"]})
+    return {k: v for k, v in res.items() if k != "runs"} | {"table": rows}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
+    ap.add_argument("--out", default=None, help="write the full result (JSON) here")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    a = sub.add_parser("sweep")
+    a.add_argument("--n", type=int, default=1000)
+    a.add_argument("--R0", type=float, default=100.0)
+    a.add_argument("--steps", type=int, default=200000)
+    a.add_argument("--check-every", type=int, default=50000)
+    a.add_argument("--stencil", type=int, default=25, choices=[9, 25])
+    a.add_argument("--xis", type=float, nargs="+", default=[-0.4, -0.2, 0.0, 0.2, 0.4])
+    a.add_argument("--betas", type=float, nargs="+", default=[0.0, 10.0, 20.0, 30.0, 45.0])
+    c = sub.add_parser("convergence")
+    c.add_argument("--radii", type=float, nargs="+", default=[12.5, 25.0, 50.0, 100.0, 200.0, 400.0])
+    c.add_argument("--t-end", type=float, default=1.0)
+    c.add_argument("--Rs", type=float, default=None)
+    args = ap.parse_args(argv)
+    if args.cmd == "sweep":
+        res = contact_angle_sweep(args.xis, args.betas, n=args.n, R0=args.R0, steps=args.steps,
+                                  check_every=args.check_every, avg_stencil=args.stencil, storage=args.storage)
+        summary = _summary_sweep(res)
+    else:
+        res = [coalescence(R0, Rs=args.Rs, t_end=args.t_end, storage=args.storage) for R0 in args.radii]
+        summary = [{k: v for k, v in r.items() if k not in ("t", "b", "max_u")} for r in res]
+    if args.out:
+        with open(args.out, "w") as fh:
+            json.dump(res, fh)
+    json.dump(summary, sys.stdout, indent=1)
+    print()
+
+
+if __name__ == "__main__":
+    main()
