@@ -39,7 +39,7 @@ bool make_geo(const lbm_params* p, Geo* g) {
 }
 
 struct Layout {
-  size_t f, P, flags, list, flist, counts, small, partial, mass, smask, stage, dpart, total;
+  size_t f, P, flags, list, imask, flist, counts, small, partial, mass, smask, stage, dpart, total;
 };
 
 constexpr int MASS_BLOCKS = 1024;
@@ -56,6 +56,7 @@ bool layout(const lbm_params* p, const Geo& g, Layout* L) {
   L->P = off;        off = align_up(off + 4 * (size_t)g.plane * cs, A);
   L->flags = off;    off = align_up(off + (size_t)g.plane * 2, A);
   L->list = off;     off = align_up(off + (size_t)cap * 4, A);
+  L->imask = off;    off = align_up(off + (size_t)cap * 4, A);
   L->flist = off;    off = align_up(off + (size_t)N * 4, A);
   L->counts = off;   off = align_up(off + (size_t)scan_blocks * 4, A);
   L->small = off;    off = align_up(off + 64, A);
@@ -116,7 +117,7 @@ lbm_status launch_density_and_virtual(lbm_ctx* c, const T* f) {
   c->p_valid = false;
   if (c->ph.bc == BC_VAVG && c->n_iface > 0) {
     s = launch(c, LBM_KC_VIRTUAL, "k_virtual_density", [&] {
-      k_virtual_density<C><<<(c->n_iface + 127) / 128, 128, 0, c->stream>>>(P, c->flags, c->iface_list,
+      k_virtual_density<C><<<(c->n_iface + 127) / 128, 128, 0, c->stream>>>(P, c->iface_mask, c->iface_list,
                                                                              c->n_iface, c->g, kphys<C>(c->ph));
     });
   }
@@ -142,7 +143,7 @@ lbm_status step_two_pass(lbm_ctx* c, int nsteps) {
     if (s) return s;
     if (c->ph.bc == BC_VAVG && c->n_iface > 0) {
       s = launch(c, LBM_KC_VIRTUAL, "k_virtual_density", [&] {
-        k_virtual_density<C><<<(c->n_iface + 127) / 128, 128, 0, c->stream>>>(P, c->flags, c->iface_list,
+        k_virtual_density<C><<<(c->n_iface + 127) / 128, 128, 0, c->stream>>>(P, c->iface_mask, c->iface_list,
                                                                                c->n_iface, c->g, kphys<C>(c->ph));
       });
       if (s) return s;
@@ -181,7 +182,7 @@ lbm_status step_fused(lbm_ctx* c, int nsteps) {
     if (c->ph.bc == BC_VAVG && c->n_iface > 0) {
       // rho~(t) of Eq. 8 into the solid cells of the plane the step reads
       s = launch(c, LBM_KC_VIRTUAL, "k_virtual_density", [&] {
-        k_virtual_density<C><<<(c->n_iface + 127) / 128, 128, 0, c->stream>>>(Pin, c->flags, c->iface_list,
+        k_virtual_density<C><<<(c->n_iface + 127) / 128, 128, 0, c->stream>>>(Pin, c->iface_mask, c->iface_list,
                                                                                c->n_iface, c->g, kphys<C>(c->ph));
       });
       if (s) return s;
@@ -324,6 +325,7 @@ lbm_status lbm_create(const lbm_params* params, void* d_workspace, size_t bytes,
   c->p_valid = false;
   c->flags = (uint16_t*)(c->ws + L.flags);
   c->iface_list = (int*)(c->ws + L.list);
+  c->iface_mask = (uint32_t*)(c->ws + L.imask);
   c->fluid_list = (int*)(c->ws + L.flist);
   c->scan_counts = (int*)(c->ws + L.counts);
   c->small = (int*)(c->ws + L.small);
@@ -402,6 +404,11 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* d_mask) {
   if (h[1] > c->if_capacity) return fail(c, LBM_ERR_SPACE, "interface-solid list exceeds max_interface");
   c->n_iface = h[1];
   c->n_fluid = h[2];
+  if (c->n_iface > 0) {
+    k_iface_mask<<<(c->n_iface + 127) / 128, 128, 0, c->stream>>>(c->flags, c->iface_list, c->n_iface, g,
+                                                                  c->iface_mask);
+    if ((s = after_launch(c, "k_iface_mask"))) return s;
+  }
   c->has_geometry = true;
   return LBM_OK;
 }

@@ -22,6 +22,7 @@ struct BatchDesc {
   const uint16_t* flags;
   const int* fluid_list;
   const int* iface_list;
+  const uint32_t* iface_mask;
   int n_fluid, n_iface;
   int cur, pcur;
   Geo g;
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(128) k_virtual_batch(const BatchDesc<C>* __res
   const BatchDesc<C>& D = d[b.x];
   const int pcur = D.pcur ^ parity;
   const int t = b.y + threadIdx.x;
-  if (t < D.n_iface) virtual_density_node<C>((C*)D.Pbuf[pcur ^ 1], D.flags, D.iface_list, t, D.g, D.ph);
+  if (t < D.n_iface) virtual_density_node<C>((C*)D.Pbuf[pcur ^ 1], D.iface_mask, D.iface_list, t, D.g, D.ph);
 }
 
 template <typename T>
@@ -165,6 +166,7 @@ void fill_descs(lbm_batch* b) {
     d.flags = c->flags;
     d.fluid_list = c->fluid_list;
     d.iface_list = c->iface_list;
+    d.iface_mask = c->iface_mask;
     d.n_fluid = c->n_fluid;
     d.n_iface = c->ph.bc == BC_VAVG ? c->n_iface : 0;
     d.cur = c->cur;

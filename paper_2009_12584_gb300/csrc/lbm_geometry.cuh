@@ -166,4 +166,25 @@ static __global__ void __launch_bounds__(SCAN_BLOCK) k_class_write(const uint16_
   }
 }
 
+// Fluid neighbours of each interface-solid cell within its 5 x 5 stencil:
+// bit (dy + 2) * 5 + (dx + 2) is set when node (x + dx, y + dy) is fluid.
+// Computed once per geometry; Eq. 8 then loads only the densities of fluid
+// neighbours (both the D2Q25 and the D2Q9 average read this mask).
+static __global__ void __launch_bounds__(128) k_iface_mask(const uint16_t* __restrict__ flags,
+                                                           const int* __restrict__ list, int n, Geo g,
+                                                           uint32_t* __restrict__ mask) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int k = list[t];
+  uint32_t m = 0;
+#pragma unroll
+  for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+    for (int dx = -2; dx <= 2; ++dx) {
+      if (dx == 0 && dy == 0) continue;
+      if (!(flags[k + dx + dy * g.px] & F_SOLID)) m |= 1u << ((dy + 2) * 5 + (dx + 2));
+    }
+  mask[t] = m;
+}
+
 }  // namespace lbm

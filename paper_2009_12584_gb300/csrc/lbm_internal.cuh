@@ -29,6 +29,7 @@ struct lbm_ctx {
   bool p_valid;        // P holds the densities of the current state (single-pass)
   uint16_t* flags;
   int* iface_list;
+  uint32_t* iface_mask; // fluid neighbours of each interface-solid cell (5 x 5 stencil bits)
   int* fluid_list;     // fluid nodes in node order, edge nodes tagged (padded indices)
   int* scan_counts;    // per-block interface counts / offsets
   int* small;          // [0] error count, [1] interface total, [2] fluid total

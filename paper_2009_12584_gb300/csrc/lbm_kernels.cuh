@@ -261,24 +261,22 @@ __global__ void __launch_bounds__(256, 4) k_collide_list(const T* __restrict__ f
 }
 
 // ---- K2: virtual solid density of Eq. 8 over the interface-solid list -----
-// All flags and densities of the stencil are loaded in one round trip; the
-// solid neighbours are then dropped by select (their density-plane values
-// are finite: zero or an earlier rho~).
+// The fluid neighbours come from the per-cell mask built with the geometry
+// (k_iface_mask); the densities of all of them are loaded in one round trip
+// before the sums.
 template <typename C, bool AVG9>
-__device__ __forceinline__ void virtual_density(const C* __restrict__ P, const uint16_t* __restrict__ flags,
-                                                const Geo& g, int k, const PhysK<C>& ph, C& v0, C& v1) {
+__device__ __forceinline__ void virtual_density(const C* __restrict__ P, uint32_t msk, const Geo& g, int k,
+                                                const PhysK<C>& ph, C& v0, C& v1) {
   constexpr int REACH = AVG9 ? 1 : 2;
   constexpr int NB = (2 * REACH + 1) * (2 * REACH + 1);
-  uint16_t fl[NB];
   C p0[NB], p1[NB];
 #pragma unroll
   for (int dy = -REACH; dy <= REACH; ++dy)
 #pragma unroll
     for (int dx = -REACH; dx <= REACH; ++dx) {
       const int j = (dy + REACH) * (2 * REACH + 1) + (dx + REACH);
-      const int m = k + dx + dy * g.px;
-      fl[j] = __ldg(flags + m);
-      ldP(P, m, p0[j], p1[j]);
+      p0[j] = p1[j] = C(0);
+      if ((msk >> ((dy + 2) * 5 + (dx + 2))) & 1u) ldP(P, k + dx + dy * g.px, p0[j], p1[j]);
     }
   C num0 = 0, num1 = 0, den = 0;
 #pragma unroll
@@ -287,7 +285,7 @@ __device__ __forceinline__ void virtual_density(const C* __restrict__ P, const u
     for (int dx = -REACH; dx <= REACH; ++dx) {
       if (dx == 0 && dy == 0) continue;
       const int j = (dy + REACH) * (2 * REACH + 1) + (dx + REACH);
-      const bool fluid = !(fl[j] & F_SOLID);
+      const bool fluid = (msk >> ((dy + 2) * 5 + (dx + 2))) & 1u;
       const int r2 = dx * dx + dy * dy;
       const C w = AVG9 ? (r2 == 1 ? C(1) / C(9) : C(1) / C(36))
                        : (r2 == 1   ? C(4) / C(21)
@@ -304,26 +302,27 @@ __device__ __forceinline__ void virtual_density(const C* __restrict__ P, const u
 }
 
 template <typename C>
-__device__ __forceinline__ void virtual_density_node(C* __restrict__ P, const uint16_t* __restrict__ flags,
+__device__ __forceinline__ void virtual_density_node(C* __restrict__ P, const uint32_t* __restrict__ mask,
                                                      const int* __restrict__ list, int t, const Geo& g,
                                                      const PhysK<C>& ph) {
   const int k = list[t];
+  const uint32_t msk = mask[t];
   C v0, v1;
   if (ph.avg9)
-    virtual_density<C, true>(P, flags, g, k, ph, v0, v1);
+    virtual_density<C, true>(P, msk, g, k, ph, v0, v1);
   else
-    virtual_density<C, false>(P, flags, g, k, ph, v0, v1);
+    virtual_density<C, false>(P, msk, g, k, ph, v0, v1);
   int x, y;
   coords(g, k, x, y);
   stP_ghosts(P, g, x, y, v0, v1);
 }
 
 template <typename C>
-__global__ void __launch_bounds__(128) k_virtual_density(C* __restrict__ P, const uint16_t* __restrict__ flags,
+__global__ void __launch_bounds__(128) k_virtual_density(C* __restrict__ P, const uint32_t* __restrict__ mask,
                                                          const int* __restrict__ list, int n, Geo g,
                                                          PhysK<C> ph) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) virtual_density_node<C>(P, flags, list, t, g, ph);
+  if (t < n) virtual_density_node<C>(P, mask, list, t, g, ph);
 }
 
 
