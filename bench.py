@@ -173,6 +173,24 @@ def cpu_baseline(target_s=15.0):
                       f"{steps} steps, {dt:.1f} s, single thread"}
 
 
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The largest value of x over all ranks (the job ends with its slowest
+    rank); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_mlups(fluid_nodes: int, steps: int, seconds: float, world: int) -> float:
+    """Whole-job MLUPS of `world` replicas that each advance `fluid_nodes`
+    nodes `steps` times, timed by the slowest rank."""
+    return world * fluid_nodes * steps / seconds / 1e6
+
+
 def run_reference(args, rank):
     """Reference arm: the FP64 oracle timed on the host cores."""
     if rank != 0:
@@ -386,14 +404,11 @@ def main():
     torch.cuda.synchronize()
     launches = sim.launch_count - l0
     clocks = sampler.stop()
-    t_ms = e0.elapsed_time(e1)
+    t_ms = max_over_ranks(e0.elapsed_time(e1), world)
     if world > 1:
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
         dist.barrier()
     ms_per_step = t_ms / args.steps
-    value = world * nf * args.steps / (t_ms / 1e3) / 1e6
+    value = replica_mlups(nf, args.steps, t_ms / 1e3, world)
 
     # dominant kernel and its roofline
     dom = max(ms_cls, key=lambda k: ms_cls[k])
@@ -410,19 +425,22 @@ def main():
                 "kernel_ms_per_step": {k: round(v / args.steps, 4) for k, v in ms_cls.items() if cnt_cls[k]}}
 
     # end to end through the host API: host buffers in, host buffers out
+    # (every rank runs it; the slowest rank's wall time counts)
     e2e = None
-    if not args.no_e2e and rank == 0:
+    if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         h_mask, h_rA, h_rB = pin(mask), pin(rA), pin(rB)
         outs = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(4)]
         sim2 = sim  # reuse the context and its workspace
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
         sim2.run_host(sim.wetting, h_mask, h_rA, h_rB, args.steps, outs)
-        t_e2e = time.perf_counter() - t0
-        h2d = mask.nbytes + rA.nbytes + rB.nbytes
-        d2h = sum(o.numel() * 8 for o in outs)
-        e2e = {"value": nf * args.steps / t_e2e / 1e6, "unit": "MLUPS",
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+        h2d = world * (mask.nbytes + rA.nbytes + rB.nbytes)  # whole job, like the value
+        d2h = world * sum(o.numel() * 8 for o in outs)
+        e2e = {"value": replica_mlups(nf, args.steps, t_e2e, world), "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "wall_s": round(t_e2e, 3),
                "what": "lbm_run_host: mask+densities H2D, geometry, init, K steps, moments D2H"}
