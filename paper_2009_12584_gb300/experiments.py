@@ -25,6 +25,8 @@ of the slope fit is b / R0 in [0.05, 1/3] after the early minimum of b
 
     python -m paper_2009_12584_gb300.experiments sweep [--n 1000 --steps 200000]
     python -m paper_2009_12584_gb300.experiments convergence [--radii 12.5 25 50 100 200 400]
+    python -m paper_2009_12584_gb300.experiments slide     # inclined walls, FP32 vs FP64
+    python -m paper_2009_12584_gb300.experiments curved    # coalescence on a disk, FP32/16 vs FP64
 """
 from __future__ import annotations
 
@@ -53,13 +55,15 @@ def tau_from_nu(nu: float) -> float:
     return 3.0 * nu + 0.5
 
 
-def wall_line(n: int, beta_deg: float, R0: float):
+def wall_line(n: int, beta_deg: float, R0: float, ny=None):
     """A point of the staircase plane of Sec. 3.1 and its direction: the line
-    y = tan(beta) (x - L/2 - R0 sin(beta)) + L/2 - R0 cos(beta), tangent to
-    the initial droplet. On a flat wall (beta = 0) the point is moved to the
-    halfway plane above the last solid row."""
+    y = tan(beta) (x - L_X/2 - R0 sin(beta)) + L_Y/2 - R0 cos(beta), tangent
+    to the initial droplet (L_X = n, L_Y = ny or n). On a flat wall
+    (beta = 0) the point is moved to the halfway plane above the last solid
+    row."""
     b = math.radians(beta_deg)
-    x0, y0 = n / 2 + R0 * math.sin(b), n / 2 - R0 * math.cos(b)
+    ly = n if ny is None else ny
+    x0, y0 = n / 2 + R0 * math.sin(b), ly / 2 - R0 * math.cos(b)
     if beta_deg == 0.0:
         y0 = math.ceil(y0) - 0.5
     return (x0, y0), beta_deg
@@ -177,6 +181,101 @@ def convergence(radii=(12.5, 25.0, 50.0, 100.0, 200.0, 400.0), *, t_end=1.0, sto
     return [coalescence(R0, t_end=t_end, storage=storage) for R0 in radii]
 
 
+def wall_sliding_study(*, nx=400, ny=200, R0=30.0, betas=(0.0, 10.0, 20.0, 30.0, 45.0), thetas=(60.0, 90.0, 120.0),
+                       bcs=("martys_chen", "llkc", "virtual_avg"), steps=50000, sample_every=500,
+                       storages=("fp32", "fp64")):
+    """A droplet of radius R0 tangent to an inclined staircase wall (Sec.
+    3.1) for every wall angle, target contact angle (parameters from the
+    linear calibration of inputs.wetting_for_angle) and wetting scheme, each
+    storage format as one batch. Samples the centre-of-mass sliding velocity
+    every ``sample_every`` steps and the contact angle at the end, and reports
+    every format's largest deviation from FP64."""
+    cases = [(bc, th, be) for bc in bcs for th in thetas for be in betas]
+    mask = {be: inputs.inclined_wall_mask(nx, ny, be, R0) for be in betas}
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, ny / 2, R0)
+    per = {}
+    for st in storages:
+        sims = []
+        for bc, th, be in cases:
+            sim = lbm.Simulation(nx, ny, storage=st)
+            sim.set_geometry(mask[be]).set_wetting(bc, **inputs.wetting_for_angle(bc, th)).init_fields(rA, rB)
+            sims.append(sim)
+        batch = lbm.Batch(sims)
+        ud = [[] for _ in cases]
+        t0 = time.time()
+        done = 0
+        while done < steps:
+            k = min(sample_every, steps - done)
+            batch.step(k)
+            done += k
+            for j, (bc, th, be) in enumerate(cases):
+                b = math.radians(be)
+                d = sims[j].diagnostics(tangent=(math.cos(b), math.sin(b)))
+                ud[j].append(d["sliding_velocity"])
+        ang = []
+        for j, (bc, th, be) in enumerate(cases):
+            wp, wa = wall_line(nx, be, R0, ny)
+            ang.append(sims[j].diagnostics(wall_point=wp, wall_angle_deg=wa)["contact_angle_deg"])
+        wall = time.time() - t0
+        batch.close()
+        for sim in sims:
+            sim.close()
+        per[st] = {"u_d": ud, "theta": ang, "wall_s": wall}
+    runs = []
+    for j, (bc, th, be) in enumerate(cases):
+        r = {"bc": bc, "theta_target": th, "beta": be}
+        for st in storages:
+            r[f"u_d_end/{st}"] = per[st]["u_d"][j][-1]
+            r[f"theta/{st}"] = per[st]["theta"][j]
+        if "fp64" in storages:
+            for st in storages:
+                if st != "fp64":
+                    r[f"max_abs_du/{st}"] = float(np.max(np.abs(np.array(per[st]["u_d"][j]) -
+                                                                np.array(per["fp64"]["u_d"][j]))))
+                    r[f"abs_dtheta/{st}"] = abs(per[st]["theta"][j] - per["fp64"]["theta"][j])
+        runs.append(r)
+    return {"nx": nx, "ny": ny, "R0": R0, "steps": steps, "sample_every": sample_every,
+            "wall_s": {st: per[st]["wall_s"] for st in storages}, "runs": runs,
+            "samples": {st: per[st]["u_d"] for st in storages}}
+
+
+def curved_coalescence_study(*, nx=800, ny=600, Rs=150.0, R0=25.0, gap=52.0, theta=60.0, steps=100000,
+                             sample_every=100, storages=("fp64", "fp32", "fp16", "bf16"), delta=8.0):
+    """Two droplets of radius R0, centres ``gap`` apart, on a convex disk of
+    radius Rs centred in a periodic box (Sec. 4), smoothed interfaces,
+    improved scheme at the target contact angle; the bridge radius on the
+    symmetry column every ``sample_every`` steps for each storage format and
+    its largest deviation from FP64."""
+    mask = inputs.circle_surface_mask(nx, ny, nx / 2, ny / 2, Rs, periodic=True)
+    yc = ny / 2 + Rs - R0 * math.cos(math.radians(theta))
+    rA, rB = inputs.tanh_droplets(nx, ny, (nx / 2 - gap / 2, nx / 2 + gap / 2), yc, R0, 1.0, 0.055, delta)
+    rA, rB = rA * (1 - mask), rB * (1 - mask)
+    xb = nx // 2
+    y0 = next(y for y in range(ny // 2, ny) if mask[y, xb] == 0 and mask[y - 1, xb] == 1)
+    wet = inputs.wetting_for_angle("virtual_avg", theta)
+    per = {}
+    for st in storages:
+        sim = lbm.Simulation(nx, ny, periodic_x=True, periodic_y=True, storage=st)
+        sim.set_geometry(mask).set_wetting("virtual_avg", **wet).init_fields(rA, rB)
+        bs, t0, done = [], time.time(), 0
+        while done < steps:
+            k = min(sample_every, steps - done)
+            sim.step(k)
+            done += k
+            bs.append(sim.diagnostics(bridge=(xb, y0))["bridge_radius"])
+        per[st] = {"b": bs, "wall_s": time.time() - t0, "mass": sim.mass().tolist()}
+        sim.close()
+    out = {"nx": nx, "ny": ny, "Rs": Rs, "R0": R0, "gap": gap, "theta": theta, "steps": steps,
+           "sample_every": sample_every, "bridge": (xb, y0), "b_end": {st: per[st]["b"][-1] for st in storages},
+           "wall_s": {st: per[st]["wall_s"] for st in storages}, "mass": {st: per[st]["mass"] for st in storages},
+           "b": {st: per[st]["b"] for st in storages}}
+    if "fp64" in storages:
+        ref = np.array(per["fp64"]["b"])
+        out["max_abs_db"] = {st: float(np.max(np.abs(np.array(per[st]["b"]) - ref))) for st in storages
+                             if st != "fp64"}
+    return out
+
+
 def _summary_sweep(res):
     rows = []
     for r in res["runs"]:
@@ -204,8 +303,20 @@ def main(argv=None):
     c.add_argument("--radii", type=float, nargs="+", default=[12.5, 25.0, 50.0, 100.0, 200.0, 400.0])
     c.add_argument("--t-end", type=float, default=1.0)
     c.add_argument("--Rs", type=float, default=None)
+    sl = sub.add_parser("slide")
+    sl.add_argument("--steps", type=int, default=50000)
+    sl.add_argument("--sample-every", type=int, default=500)
+    cu = sub.add_parser("curved")
+    cu.add_argument("--steps", type=int, default=100000)
+    cu.add_argument("--sample-every", type=int, default=100)
     args = ap.parse_args(argv)
-    if args.cmd == "sweep":
+    if args.cmd == "slide":
+        res = wall_sliding_study(steps=args.steps, sample_every=args.sample_every)
+        summary = {k: v for k, v in res.items() if k != "samples"}
+    elif args.cmd == "curved":
+        res = curved_coalescence_study(steps=args.steps, sample_every=args.sample_every)
+        summary = {k: v for k, v in res.items() if k != "b"}
+    elif args.cmd == "sweep":
         res = contact_angle_sweep(args.xis, args.betas, n=args.n, R0=args.R0, steps=args.steps,
                                   check_every=args.check_every, avg_stencil=args.stencil, storage=args.storage)
         summary = _summary_sweep(res)

@@ -34,3 +34,18 @@ def test_short_coalescence_bridge_grows():
     assert b[-1] > 2.0 and b[-1] == max(b)
     half = b[len(b) // 2:]
     assert all(half[i + 1] >= half[i] for i in range(len(half) - 1))
+
+
+def test_small_wall_sliding_study_fp32_tracks_fp64():
+    res = ex.wall_sliding_study(nx=120, ny=70, R0=12.0, betas=(0.0, 20.0), thetas=(60.0,),
+                                bcs=("martys_chen", "virtual_avg"), steps=800, sample_every=200)
+    assert len(res["runs"]) == 4
+    for r in res["runs"]:
+        assert r["max_abs_du/fp32"] < 1e-6 and r["abs_dtheta/fp32"] < 0.5, r
+
+
+def test_small_curved_coalescence_study():
+    res = ex.curved_coalescence_study(nx=200, ny=160, Rs=40.0, R0=10.0, gap=22.0, steps=600, sample_every=100,
+                                      storages=("fp64", "fp32"))
+    assert len(res["b"]["fp64"]) == 6 and res["bridge"][1] > 80
+    assert res["max_abs_db"]["fp32"] < 1e-3
