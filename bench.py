@@ -360,6 +360,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the fp16/bf16, batched and accuracy arms")
+    ap.add_argument("--l2-fetch", type=int, default=32, choices=[0, 32, 64, 128],
+                    help="L2 fetch granularity hint for this process (0: leave the CUDA default)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -378,6 +380,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
+    l2_prev = lbm.set_l2_fetch_granularity(args.l2_fetch) if args.l2_fetch else None
 
     n = args.n
     mask, rA, rB = workload(n)
@@ -474,7 +477,8 @@ def main():
                            "l2": "inputs larger than L2 (populations %.1f GB per buffer)"
                                  % (18 * n * n * BYTES_PER_UPDATE[args.storage] / 144 * 4 / 1e9),
                            "all_node_mlups": round(world * n * n * args.steps / (t_ms / 1e3) / 1e6, 1),
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"replicas x{world}",
+                           "l2_fetch_granularity_bytes": args.l2_fetch or l2_prev},
                 "roofline": roofline, "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu, **extra}
         print(json.dumps(line), flush=True)

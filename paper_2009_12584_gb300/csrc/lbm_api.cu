@@ -555,6 +555,15 @@ lbm_status lbm_mass(lbm_ctx* c, double* h_out) {
   return s;
 }
 
+lbm_status lbm_set_l2_fetch_granularity(int32_t bytes, int32_t* previous) {
+  if (bytes != 32 && bytes != 64 && bytes != 128) return LBM_ERR_ARG;
+  size_t old = 0;
+  if (cudaDeviceGetLimit(&old, cudaLimitMaxL2FetchGranularity) != cudaSuccess) return LBM_ERR_CUDA;
+  if (cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes) != cudaSuccess) return LBM_ERR_CUDA;
+  if (previous) *previous = (int32_t)old;
+  return LBM_OK;
+}
+
 lbm_status lbm_diagnostics(lbm_ctx* c, const lbm_diag_params* p, lbm_diag* h_out) {
   if (!c || !p || !h_out) return LBM_ERR_ARG;
   if (!c->has_geometry || !c->has_fields) return fail(c, LBM_ERR_STATE, "lbm_diagnostics before geometry and fields");

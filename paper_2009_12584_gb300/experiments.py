@@ -310,6 +310,7 @@ def main(argv=None):
     cu.add_argument("--steps", type=int, default=100000)
     cu.add_argument("--sample-every", type=int, default=100)
     args = ap.parse_args(argv)
+    lbm.set_l2_fetch_granularity(32)  # fastest for the step (lbm_set_l2_fetch_granularity)
     if args.cmd == "slide":
         res = wall_sliding_study(steps=args.steps, sample_every=args.sample_every)
         summary = {k: v for k, v in res.items() if k != "samples"}

@@ -65,7 +65,8 @@ class LbmDiag(ctypes.Structure):
 EXPORTS = [
     "lbm_workspace_bytes", "lbm_create", "lbm_set_stream", "lbm_set_geometry", "lbm_set_wetting",
     "lbm_init_fields", "lbm_step", "lbm_step_profiled", "lbm_moments", "lbm_forces", "lbm_get_populations",
-    "lbm_set_populations", "lbm_mass", "lbm_diagnostics", "lbm_interface_count", "lbm_sync", "lbm_run_host",
+    "lbm_set_populations", "lbm_mass", "lbm_diagnostics", "lbm_set_l2_fetch_granularity", "lbm_interface_count",
+    "lbm_sync", "lbm_run_host",
     "lbm_destroy", "lbm_status_str", "lbm_last_error", "lbm_launch_count",
     "lbm_batch_workspace_bytes", "lbm_batch_create", "lbm_batch_set_graph_steps", "lbm_batch_step",
     "lbm_batch_autotune", "lbm_batch_launch_count", "lbm_batch_last_error", "lbm_batch_destroy",
@@ -116,6 +117,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "lbm_set_populations": [vp, dp],
             "lbm_mass": [vp, ctypes.POINTER(ctypes.c_double)],
             "lbm_diagnostics": [vp, ctypes.POINTER(LbmDiagParams), ctypes.POINTER(LbmDiag)],
+            "lbm_set_l2_fetch_granularity": [i32, ctypes.POINTER(i32)],
             "lbm_interface_count": [vp, ctypes.POINTER(i64)],
             "lbm_sync": [vp],
             "lbm_run_host": [vp, W, vp, vp, vp, i32, vp, vp, vp, vp],
@@ -149,6 +151,20 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.lbm_batch_last_error.restype = ctypes.c_char_p
         _lib = lib
         return lib
+
+
+def set_l2_fetch_granularity(nbytes: int) -> int:
+    """Set the L2 fetch granularity hint of the current CUDA device's context
+    (32, 64 or 128 bytes; lbm_set_l2_fetch_granularity) and return the
+    previous value. It applies to every kernel of this process on that
+    device; the library never sets it by itself. 32 bytes is fastest for the
+    step on porous geometries."""
+    lib = load()
+    prev = ctypes.c_int32()
+    st = lib.lbm_set_l2_fetch_granularity(int(nbytes), ctypes.byref(prev))
+    if st != OK:
+        raise LbmError(st, "lbm_set_l2_fetch_granularity")
+    return prev.value
 
 
 def make_params(nx, ny, *, tau=(1.0, 1.0), G_AB=3.0, periodic_x=False, periodic_y=False,

@@ -358,3 +358,23 @@ def test_batch_autotune_and_members_stay_usable():
     for s, m in zip(sims, m0):
         np.testing.assert_allclose(s.mass(), m, rtol=1e-5)
         s.step(1)  # members can still be stepped alone
+
+
+def test_l2_fetch_granularity_hint_changes_no_result():
+    nx, ny = 96, 64
+    mask = inputs.inclined_wall_mask(nx, ny, 20.0, 10)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, ny / 2, 10)
+    outs = []
+    prev = lbm.set_l2_fetch_granularity(128)
+    try:
+        for g in (128, 32):
+            assert lbm.set_l2_fetch_granularity(g) in (32, 64, 128)
+            s = lbm.Simulation(nx, ny, storage="fp32")
+            s.set_geometry(mask).set_wetting("virtual_avg", G_s=(3.0, 3.0), chi=(1.2, 0.8)).init_fields(rA, rB)
+            outs.append(s.step(30).populations())
+        assert torch.equal(outs[0], outs[1])
+        with pytest.raises(lbm.LbmError):
+            lbm.set_l2_fetch_granularity(48)
+        assert lbm.set_l2_fetch_granularity(prev) == 32
+    finally:
+        lbm.set_l2_fetch_granularity(prev)
