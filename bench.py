@@ -259,13 +259,16 @@ def run_single(n, mask, rA, rB, nf, storage, kernel, steps, warmup):
     return out
 
 
-def run_batched(storage, steps, warmup, nsims=512):
+def run_batched(storage, steps, warmup, nsims=512, l2_fetch=128):
     """512 independent inclined-wall simulations (sizes 64x64 ... 512x256,
     wall angle 0 ... 45 deg, contact angle 45 ... 135 deg, three schemes mixed,
     seed 0) advanced together by one batch; steps per graph replay and
-    threads per block picked by the autotuner."""
+    threads per block picked by the autotuner. Their single straight walls
+    leave long fluid segments, which stream best with 128-byte L2 fetches
+    (the porous arms use 32); the previous setting is restored after."""
     import torch
     from paper_2009_12584_gb300 import inputs, lbm
+    l2_prev = lbm.set_l2_fetch_granularity(l2_fetch)
     t0 = time.time()
     work = inputs.batched_workload(nsims, seed=0)
     sims = []
@@ -292,10 +295,11 @@ def run_batched(storage, steps, warmup, nsims=512):
            "sims": nsims, "fluid_nodes": nf, "threads_per_block": choice[0], "steps_per_graph": choice[1],
            "gpu_launches": b.launch_count - l0, "setup_s": round(setup, 1),
            "workload": "512 inclined-wall simulations, 64x64..512x256, beta U[0,45], theta U[45,135], "
-                       "MC/LLKC/improved mixed, seed 0"}
+                       "MC/LLKC/improved mixed, seed 0", "l2_fetch_granularity_bytes": l2_fetch}
     b.close()
     del sims, b
     torch.cuda.empty_cache()
+    lbm.set_l2_fetch_granularity(l2_prev)
     return out
 
 
