@@ -27,6 +27,8 @@ of the slope fit is b / R0 in [0.05, 1/3] after the early minimum of b
     python -m paper_2009_12584_gb300.experiments convergence [--radii 12.5 25 50 100 200 400]
     python -m paper_2009_12584_gb300.experiments slide     # inclined walls, FP32 vs FP64
     python -m paper_2009_12584_gb300.experiments curved    # coalescence on a disk, FP32/16 vs FP64
+    python -m paper_2009_12584_gb300.experiments curvature # Fig. 8A: b(t) on disks of several radii
+    python -m paper_2009_12584_gb300.experiments viscosity # Fig. 8B: b(t) at several viscosities
 """
 from __future__ import annotations
 
@@ -108,7 +110,7 @@ def contact_angle_sweep(xis=(-0.4, -0.2, 0.0, 0.2, 0.4), betas=(0.0, 10.0, 20.0,
             "wall_s": wall, "runs": out}
 
 
-def coalescence_setup(R0: float, *, Rs=None, theta_c=THETA_C, Oh=OH, sigma=SIGMA, delta=8.0):
+def coalescence_setup(R0: float, *, Rs=None, theta_c=THETA_C, Oh=OH, sigma=SIGMA, delta=8.0, nu=None):
     """Grid, mask, initial densities and parameters of the Sec. 4 runs: box
     14 R0 x 10 R0; surface (x - L_X/2)^2 + (y - (L_Y/2 - Rs))^2 = Rs^2, or
     the half plane y < L_Y/2 for Rs = None; droplets centred at
@@ -126,7 +128,8 @@ def coalescence_setup(R0: float, *, Rs=None, theta_c=THETA_C, Oh=OH, sigma=SIGMA
     rA, rB = inputs.tanh_droplets(nx, ny, (nx / 2 - dx, nx / 2 + dx), ny / 2 - R0 * math.cos(th), R0,
                                   1.0, 0.055, delta)
     rA, rB = rA * (1 - mask), rB * (1 - mask)
-    nu = Oh * math.sqrt(sigma * R0)
+    if nu is None:
+        nu = Oh * math.sqrt(sigma * R0)
     xb = nx // 2
     col = mask[:, xb]
     # first fluid node above the surface, whose top is at y = L_Y / 2
@@ -151,9 +154,11 @@ def viscous_slope(t, b, R0, tau_visc, window=(0.05, 1.0 / 3.0)):
     return float(np.polyfit(np.log(t[sel] / tau_visc), np.log(b[sel] / R0), 1)[0])
 
 
-def coalescence(R0: float, *, Rs=None, t_end=1.0, samples=200, storage="fp32", xi=XI_C, theta_c=THETA_C):
-    """b(t) of two coalescing droplets up to t_end viscous times."""
-    s = coalescence_setup(R0, Rs=Rs, theta_c=theta_c)
+def coalescence(R0: float, *, Rs=None, t_end=1.0, samples=200, storage="fp32", xi=XI_C, theta_c=THETA_C,
+                nu=None):
+    """b(t) of two coalescing droplets up to t_end viscous times (nu: the
+    kinematic viscosity, else the one of Oh = 0.286)."""
+    s = coalescence_setup(R0, Rs=Rs, theta_c=theta_c, nu=nu)
     sim = lbm.Simulation(s["nx"], s["ny"], tau=(s["tau"], s["tau"]), periodic_x=True, storage=storage)
     sim.set_geometry(s["mask"]).set_wetting("virtual_avg", G_s=(3.0, 3.0), chi=chi_from_xi(xi))
     sim.init_fields(s["rhoA"], s["rhoB"])
@@ -179,6 +184,45 @@ def coalescence(R0: float, *, Rs=None, t_end=1.0, samples=200, storage="fp32", x
 
 def convergence(radii=(12.5, 25.0, 50.0, 100.0, 200.0, 400.0), *, t_end=1.0, storage="fp32"):
     return [coalescence(R0, t_end=t_end, storage=storage) for R0 in radii]
+
+
+def _crossover(r, frac=1.0 / 3.0):
+    """First time (in viscous times) at which b reaches frac * R0."""
+    for t, b in zip(r["t"], r["b"]):
+        if b >= frac * r["R0"]:
+            return t / r["tau_visc"]
+    return None
+
+
+def curvature_study(surfaces=(None, 1200.0, 400.0, 200.0, 100.0), *, R0=100.0, t_end=6.0, samples=300,
+                    storage="fp32"):
+    """Sec. 4, Fig. 8A: coalescence at Oh = 0.286 (R0 = 100, nu = 0.46) on a
+    flat surface and on disks of radius Rs. Per surface: the viscous slope,
+    the time at which b reaches R0/3 and the final bridge radius."""
+    out = []
+    for Rs in surfaces:
+        r = coalescence(R0, Rs=Rs, t_end=t_end, samples=samples, storage=storage)
+        r["t_third"] = _crossover(r)
+        r["b_end_over_R0"] = r["b"][-1] / R0
+        out.append(r)
+    return out
+
+
+def viscosity_study(nus=(0.16, 0.46, 0.92), surfaces=(None, 100.0), *, R0=100.0, t_end=6.0, samples=300,
+                    storage="fp32"):
+    """Sec. 4, Fig. 8B: coalescence at several viscosities on a flat surface
+    and on a disk of radius 100. Per run: the viscous slope, the time at which
+    b reaches R0/3, and the number of times b decreases after its first
+    maximum (the oscillations of the inertial regime)."""
+    out = []
+    for Rs in surfaces:
+        for nu in nus:
+            r = coalescence(R0, Rs=Rs, t_end=t_end, samples=samples, storage=storage, nu=nu)
+            r["t_third"] = _crossover(r)
+            b = np.asarray(r["b"])
+            r["decreases"] = int(np.sum(np.diff(b) < -1e-3))
+            out.append(r)
+    return out
 
 
 def wall_sliding_study(*, nx=400, ny=200, R0=30.0, betas=(0.0, 10.0, 20.0, 30.0, 45.0), thetas=(60.0, 90.0, 120.0),
@@ -303,6 +347,10 @@ def main(argv=None):
     c.add_argument("--radii", type=float, nargs="+", default=[12.5, 25.0, 50.0, 100.0, 200.0, 400.0])
     c.add_argument("--t-end", type=float, default=1.0)
     c.add_argument("--Rs", type=float, default=None)
+    cv = sub.add_parser("curvature")
+    cv.add_argument("--t-end", type=float, default=6.0)
+    vs = sub.add_parser("viscosity")
+    vs.add_argument("--t-end", type=float, default=6.0)
     sl = sub.add_parser("slide")
     sl.add_argument("--steps", type=int, default=50000)
     sl.add_argument("--sample-every", type=int, default=500)
@@ -311,7 +359,11 @@ def main(argv=None):
     cu.add_argument("--sample-every", type=int, default=100)
     args = ap.parse_args(argv)
     lbm.set_l2_fetch_granularity(32)  # fastest for the step (lbm_set_l2_fetch_granularity)
-    if args.cmd == "slide":
+    if args.cmd in ("curvature", "viscosity"):
+        res = (curvature_study(t_end=args.t_end, storage=args.storage) if args.cmd == "curvature"
+               else viscosity_study(t_end=args.t_end, storage=args.storage))
+        summary = [{k: v for k, v in r.items() if k not in ("t", "b", "max_u")} for r in res]
+    elif args.cmd == "slide":
         res = wall_sliding_study(steps=args.steps, sample_every=args.sample_every)
         summary = {k: v for k, v in res.items() if k != "samples"}
     elif args.cmd == "curved":

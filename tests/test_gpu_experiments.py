@@ -49,3 +49,12 @@ def test_small_curved_coalescence_study():
                                       storages=("fp64", "fp32"))
     assert len(res["b"]["fp64"]) == 6 and res["bridge"][1] > 80
     assert res["max_abs_db"]["fp32"] < 1e-3
+
+
+def test_small_curvature_and_viscosity_studies():
+    cu = ex.curvature_study(surfaces=(None, 40.0), R0=12.5, t_end=2.0, samples=20)
+    vi = ex.viscosity_study(nus=(0.16, 0.3), surfaces=(None,), R0=12.5, t_end=2.0, samples=20)
+    for r in cu + vi:
+        assert len(r["b"]) >= 20 and max(r["b"]) > 0.0 and all(math.isfinite(b) for b in r["b"])
+    assert [r["Rs"] for r in cu] == [None, 40.0]
+    assert abs(vi[1]["nu"] - 0.3) < 1e-12 and vi[1]["steps"] > vi[0]["steps"]  # tau_nu grows with nu
