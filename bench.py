@@ -41,11 +41,7 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def chi_from_xi(xi):
-    """chi of Eq. 8 as passed to the library for the paper's xi: the paper's
-    convention (xi < 0 hydrophilic) with the force of Eq. 7 taken as
-    printed corresponds to chi^A = 1 - xi, chi^B = 1 + xi."""
-    return (1.0 - xi, 1.0 + xi)
+from paper_2009_12584_gb300.experiments import chi_from_xi  # noqa: E402  (xi -> chi reading)
 
 
 def workload(n, cache=True):
