@@ -263,7 +263,18 @@ __global__ void __launch_bounds__(256, 4) k_collide_list(const T* __restrict__ f
 // ---- K2: virtual solid density of Eq. 8 over the interface-solid list -----
 // The fluid neighbours come from the per-cell mask built with the geometry
 // (k_iface_mask); the densities of all of them are loaded in one round trip
-// before the sums.
+// before the sums. The 5 x 5 stencil reads around scattered cells use up
+// whole 128-byte lines, so these loads ask L2 for 128-byte fetches whatever
+// the context's fetch granularity (the pulls of the other passes run best
+// with 32-byte fetches).
+template <typename C>
+__device__ __forceinline__ void ldP_line(const C* __restrict__ P, int64_t k, C& a, C& b) {
+  if constexpr (sizeof(C) == 4)
+    asm("ld.global.nc.L2::128B.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "l"(P + 2 * k));
+  else
+    asm("ld.global.nc.L2::128B.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(P + 2 * k));
+}
+
 template <typename C, bool AVG9>
 __device__ __forceinline__ void virtual_density(const C* __restrict__ P, uint32_t msk, const Geo& g, int k,
                                                 const PhysK<C>& ph, C& v0, C& v1) {
@@ -276,7 +287,7 @@ __device__ __forceinline__ void virtual_density(const C* __restrict__ P, uint32_
     for (int dx = -REACH; dx <= REACH; ++dx) {
       const int j = (dy + REACH) * (2 * REACH + 1) + (dx + REACH);
       p0[j] = p1[j] = C(0);
-      if ((msk >> ((dy + 2) * 5 + (dx + 2))) & 1u) ldP(P, k + dx + dy * g.px, p0[j], p1[j]);
+      if ((msk >> ((dy + 2) * 5 + (dx + 2))) & 1u) ldP_line(P, k + dx + dy * g.px, p0[j], p1[j]);
     }
   C num0 = 0, num1 = 0, den = 0;
 #pragma unroll
