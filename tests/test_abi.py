@@ -68,6 +68,11 @@ int main(void) {
          offsetof(lbm_params, storage), offsetof(lbm_params, rho_ref), offsetof(lbm_params, max_interface));
   printf("%zu %zu %zu %zu\n", sizeof(lbm_wetting_params), offsetof(lbm_wetting_params, G_s),
          offsetof(lbm_wetting_params, chi), offsetof(lbm_wetting_params, rho_s));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(lbm_diag_params), offsetof(lbm_diag_params, tangent),
+         offsetof(lbm_diag_params, box), offsetof(lbm_diag_params, bridge_x), offsetof(lbm_diag_params, bridge_y0));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(lbm_diag), offsetof(lbm_diag, com_velocity),
+         offsetof(lbm_diag, max_u), offsetof(lbm_diag, contour_points), offsetof(lbm_diag, circle),
+         offsetof(lbm_diag, bridge_radius));
   return 0;
 }
 '''
@@ -82,3 +87,19 @@ int main(void) {
     P, W = lbm.LbmParams, lbm.LbmWetting
     assert a == [ctypes.sizeof(P), P.tau.offset, P.storage.offset, P.rho_ref.offset, P.max_interface.offset]
     assert b == [ctypes.sizeof(W), W.G_s.offset, W.chi.offset, W.rho_s.offset]
+    c = [int(v) for v in out[2].split()]
+    d = [int(v) for v in out[3].split()]
+    DP, D = lbm.LbmDiagParams, lbm.LbmDiag
+    assert c == [ctypes.sizeof(DP), DP.tangent.offset, DP.box.offset, DP.bridge_x.offset, DP.bridge_y0.offset]
+    assert d == [ctypes.sizeof(D), D.com_velocity.offset, D.max_u.offset, D.contour_points.offset,
+                 D.circle.offset, D.bridge_radius.offset]
+
+
+def test_argument_checks_before_any_cuda_call(lib):
+    lib.lbm_set_l2_fetch_granularity.argtypes = [ctypes.c_int32, ctypes.c_void_p]
+    lib.lbm_set_l2_fetch_granularity.restype = ctypes.c_int
+    for bad in (0, 16, 48, 256):
+        assert lib.lbm_set_l2_fetch_granularity(bad, None) == lbm.ERR_ARG
+    lib.lbm_diagnostics.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.lbm_diagnostics.restype = ctypes.c_int
+    assert lib.lbm_diagnostics(None, None, None) == lbm.ERR_ARG
