@@ -12,9 +12,11 @@ densities of Eq. 8 within 4, so the frame and the cut do not reach the
 interior.
 
 Tolerances. FP32: the GPU's step rounds each result a few times in FP32 on
-values below 0.5 (one FP32 unit at 0.5 is 6e-8): 1e-6. FP16: the stored
-deviation from w_i rho_ref is rounded to 11 significant bits, at most
-2^-11 x 0.5 = 2.4e-4 for |f| < 0.5, plus the FP32 term: 2.5e-4."""
+values below 0.5 (one FP32 unit at 0.5 is 6e-8): 1e-6 (also for the
+single-pass schedule). FP16: the stored deviation from w_i rho_ref is
+rounded to 11 significant bits, at most 2^-11 x 0.5 = 2.4e-4 for |f| < 0.5,
+plus the FP32 term: 2.5e-4. BF16: 8 significant bits, 2^-8 x 0.5 = 2.0e-3:
+2.5e-3."""
 import numpy as np
 import pytest
 
@@ -60,12 +62,13 @@ def _windows(mask, rA, count=4, seed=7):
     return out
 
 
-@pytest.mark.parametrize("storage,tol", [("fp32", 1e-6), ("fp16", 2.5e-4)])
-def test_full_size_step_matches_oracle_on_windows(workload, storage, tol):
+@pytest.mark.parametrize("storage,kernel,tol", [("fp32", "auto", 1e-6), ("fp16", "auto", 2.5e-4),
+                                                ("bf16", "auto", 2.5e-3), ("fp32", "fused", 1e-6)])
+def test_full_size_step_matches_oracle_on_windows(workload, storage, kernel, tol):
     mask, rA, rB = workload
     wins = _windows(mask, rA)
     assert len(wins) == 4
-    sim = lbm.Simulation(N, N, periodic_x=True, periodic_y=True, storage=storage)
+    sim = lbm.Simulation(N, N, periodic_x=True, periodic_y=True, storage=storage, kernel=kernel)
     sim.set_geometry(mask).set_wetting("virtual_avg", G_s=(3.0, 3.0), chi=CHI).init_fields(rA, rB).step(STEPS)
 
     def cut():
