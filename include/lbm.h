@@ -224,7 +224,8 @@ lbm_status lbm_set_l2_fetch_granularity(int32_t bytes, int32_t* previous);
  *    halfway wall (half a node below bridge_y0, the first fluid node above
  *    the surface) to the first point above it where rho^A drops through
  *    `level`; 0 while rho^A(bridge_x, bridge_y0) < level;
- *  - max |u| over fluid nodes (the spurious-current level of Sec. 4).
+ *  - max |u| over fluid nodes (the spurious-current level of Sec. 4), and the
+ *    number of fluid nodes whose moments are not finite (a diverged run).
  * Sums are FP64 in a fixed order (deterministic); the 3x3 normal equations of
  * the fit are solved on the host. Contour edges do not wrap periodic axes. */
 typedef struct {
@@ -249,6 +250,9 @@ typedef struct {
   double circle[3];        /* xc, yc, R of the fit (NaN with fewer than 3 points) */
   double contact_angle_deg;/* through the A phase (NaN without a circle) */
   double bridge_radius;    /* 0 if not measured */
+  int64_t nonfinite_nodes; /* fluid nodes whose rho^A, rho^B or u is NaN or infinite (a run
+                              that has diverged); they are left out of every other quantity and
+                              max_u is NaN when there are any */
 } lbm_diag;
 
 /* Fill *h_out (host) for the current state. Uses the workspace's staging

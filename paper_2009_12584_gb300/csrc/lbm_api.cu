@@ -609,11 +609,12 @@ lbm_status lbm_diagnostics(lbm_ctx* c, const lbm_diag_params* p, lbm_diag* h_out
   o.com_velocity[0] = q[0] > 0 ? q[3] / q[0] : nan;
   o.com_velocity[1] = q[0] > 0 ? q[4] / q[0] : nan;
   o.sliding_velocity = o.com_velocity[0] * p->tangent[0] + o.com_velocity[1] * p->tangent[1];
-  o.max_u = sqrt(q[14]);
+  o.nonfinite_nodes = (int64_t)q[15];
+  o.max_u = q[15] > 0 ? nan : sqrt(q[14]);
   o.contour_points = (int64_t)q[5];
   o.circle[0] = o.circle[1] = o.circle[2] = nan;
   o.contact_angle_deg = nan;
-  o.bridge_radius = q[15];
+  o.bridge_radius = q[16];
   if (q[5] >= 3) {
     // normal equations of min sum (x^2 + y^2 - A x - B y - C)^2 (Kasa fit),
     // solved by Gaussian elimination with partial pivoting

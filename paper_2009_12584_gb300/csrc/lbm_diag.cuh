@@ -13,9 +13,10 @@ constexpr int DIAG_THREADS = 256;
 // reduced quantities: 0 sum w, 1 sum w x, 2 sum w y, 3 sum w u_x,
 // 4 sum w u_y, 5 crossings kept, 6..13 the Kasa sums over kept crossings
 // (x, y, xx, yy, xy, x r, y r, r with r = x^2 + y^2, coordinates relative to
-// the grid centre), 14 max |u|^2, 15 bridge radius (final kernel only)
-constexpr int DIAG_NQ = 16;
-constexpr int DIAG_NRED = 15;  // quantities reduced over nodes (0..14)
+// the grid centre), 14 max |u|^2 over finite nodes, 15 fluid nodes whose
+// rho^A, rho^B or u is not finite, 16 bridge radius (final kernel only)
+constexpr int DIAG_NQ = 17;
+constexpr int DIAG_NRED = 16;  // quantities reduced over nodes (0..15)
 
 struct DiagArgs {
   double level, rho_out;
@@ -63,6 +64,10 @@ static __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(const doub
     const int k = g.idx(x, y);
     if (flags[k] & F_SOLID) continue;
     const double rA = st[n], ux = st[2 * N + n], uy = st[3 * N + n];
+    if (!isfinite(rA) || !isfinite(st[N + n]) || !isfinite(ux) || !isfinite(uy)) {
+      acc[15] += 1.0;  // counted, and left out of every other sum
+      continue;
+    }
     const double w = fmax(rA - a.rho_out, 0.0);
     acc[0] += w;
     acc[1] += w * x;
@@ -126,7 +131,7 @@ static __global__ void k_diag_final(const double* __restrict__ partial, const do
         }
       }
     }
-    out[15] = br;
+    out[16] = br;
   }
 }
 

@@ -58,7 +58,7 @@ class LbmDiag(ctypes.Structure):
         ("com_velocity", ctypes.c_double * 2), ("sliding_velocity", ctypes.c_double),
         ("max_u", ctypes.c_double), ("contour_points", ctypes.c_int64),
         ("circle", ctypes.c_double * 3), ("contact_angle_deg", ctypes.c_double),
-        ("bridge_radius", ctypes.c_double),
+        ("bridge_radius", ctypes.c_double), ("nonfinite_nodes", ctypes.c_int64),
     ]
 
 
@@ -322,6 +322,7 @@ class Simulation:
             "sliding_velocity": o.sliding_velocity, "max_u": o.max_u,
             "contour_points": o.contour_points, "circle": (o.circle[0], o.circle[1], o.circle[2]),
             "contact_angle_deg": o.contact_angle_deg, "bridge_radius": o.bridge_radius,
+            "nonfinite_nodes": o.nonfinite_nodes,
         }
 
     def interface_count(self):

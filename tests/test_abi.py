@@ -73,6 +73,7 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(lbm_diag), offsetof(lbm_diag, com_velocity),
          offsetof(lbm_diag, max_u), offsetof(lbm_diag, contour_points), offsetof(lbm_diag, circle),
          offsetof(lbm_diag, bridge_radius));
+  printf("%zu\n", offsetof(lbm_diag, nonfinite_nodes));
   return 0;
 }
 '''
@@ -93,6 +94,7 @@ int main(void) {
     assert c == [ctypes.sizeof(DP), DP.tangent.offset, DP.box.offset, DP.bridge_x.offset, DP.bridge_y0.offset]
     assert d == [ctypes.sizeof(D), D.com_velocity.offset, D.max_u.offset, D.contour_points.offset,
                  D.circle.offset, D.bridge_radius.offset]
+    assert int(out[4]) == D.nonfinite_nodes.offset
 
 
 def test_argument_checks_before_any_cuda_call(lib):

@@ -125,3 +125,20 @@ def test_diag_deterministic_and_errors():
     # no contour inside an empty box: no circle
     d = sim.diagnostics(box=(1000.0, 1001.0, 0.0, 1.0))
     assert d["contour_points"] == 0 and math.isnan(d["contact_angle_deg"])
+
+
+def test_diag_counts_nonfinite_nodes():
+    # a diverged run, made on the host: one fluid node's populations set to NaN
+    nx, ny = 64, 40
+    mask = inputs.flat_wall_mask(nx, ny)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, 0.5, 12)
+    sim = lbm.Simulation(nx, ny, periodic_x=True, storage="fp32")
+    sim.set_geometry(mask).set_wetting("martys_chen", G_s=(-0.2, 0.2)).init_fields(rA, rB).step(20)
+    d0 = sim.diagnostics()
+    assert d0["nonfinite_nodes"] == 0 and math.isfinite(d0["max_u"])
+    f = sim.populations()
+    f[:, :, 20, 10] = float("nan")
+    sim.set_populations(f)
+    d1 = sim.diagnostics()
+    assert d1["nonfinite_nodes"] >= 1 and math.isnan(d1["max_u"])
+    assert math.isfinite(d1["weight"])  # the other sums leave those nodes out
