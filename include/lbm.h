@@ -84,12 +84,21 @@ typedef enum {
 /* Kernel schedule for lbm_step. TWO_PASS: a density pass, the virtual
  * density pass, then one fused force+collide+stream pull kernel. FUSED: one
  * kernel per step that also writes the densities of the next step (the
- * density plane is double-buffered). AUTO picks the schedule measured
- * fastest on GB300 (currently TWO_PASS). */
+ * density plane is double-buffered), warps marching up column strips.
+ * TILED: the same single-pass contract on 32 x 12 tiles, one CTA per
+ * tile, each a compacted list of its fluid nodes plus the one-node ring
+ * around it (computed again), built by lbm_set_geometry (workspace grows by
+ * 2 bytes per ring-extended region slot, about 2.5 bytes per node, for 4-
+ * and 8-byte storage). FUSED and TILED keep 4- and 8-byte populations only;
+ * FP16/BF16 storage runs TWO_PASS under any choice. All schedules give the
+ * same results bit for bit. AUTO picks the schedule measured fastest on
+ * GB300 under the library's default settings (currently TWO_PASS; TILED
+ * moves 30% fewer bytes but ties with it in time). */
 typedef enum {
   LBM_KERNEL_AUTO = 0,
   LBM_KERNEL_TWO_PASS = 1,
-  LBM_KERNEL_FUSED = 2
+  LBM_KERNEL_FUSED = 2,
+  LBM_KERNEL_TILED = 3
 } lbm_kernel;
 
 typedef struct {

@@ -39,8 +39,14 @@ bool make_geo(const lbm_params* p, Geo* g) {
 }
 
 struct Layout {
-  size_t f, P, flags, list, imask, flist, counts, small, partial, mass, smask, stage, dpart, total;
+  size_t f, P, flags, list, imask, flist, tent, toff, tnown, counts, small, partial, mass, smask, stage, dpart,
+      total;
 };
+
+// Whether a context keeps the per-tile lists of the tiled schedule.
+bool uses_tiles(const lbm_params* p) {
+  return p->kernel == LBM_KERNEL_TILED && (p->storage == LBM_STORE_FP32 || p->storage == LBM_STORE_FP64);
+}
 
 constexpr int MASS_BLOCKS = 1024;
 
@@ -58,6 +64,10 @@ bool layout(const lbm_params* p, const Geo& g, Layout* L) {
   L->list = off;     off = align_up(off + (size_t)cap * 4, A);
   L->imask = off;    off = align_up(off + (size_t)cap * 4, A);
   L->flist = off;    off = align_up(off + (size_t)N * 4, A);
+  const int64_t nt = uses_tiles(p) ? tile_count(g) : 0;
+  L->tent = off;     off = align_up(off + (size_t)nt * TILE_RS * 2, A);
+  L->toff = off;     off = align_up(off + (size_t)(nt ? nt + 1 : 0) * 4, A);
+  L->tnown = off;    off = align_up(off + (size_t)nt * 4, A);
   L->counts = off;   off = align_up(off + (size_t)scan_blocks * 4, A);
   L->small = off;    off = align_up(off + 64, A);
   L->partial = off;  off = align_up(off + 2 * MASS_BLOCKS * 8, A);
@@ -188,9 +198,16 @@ lbm_status step_fused(lbm_ctx* c, int nsteps) {
       if (s) return s;
     }
     lbm_status ls = LBM_OK;
-    s = launch(c, LBM_KC_FUSED, "k_march", [&] {
-      ls = launch_fused<T>(c->g, c->ph, fin, fout, Pin, Pout, c->flags, c->num_sms, c->stream);
-    });
+    if (c->n_tiles > 0) {
+      s = launch(c, LBM_KC_FUSED, "k_tile", [&] {
+        ls = launch_tiled<T>(c->g, c->ph, fin, fout, Pin, Pout, c->flags, c->tile_entries, c->tile_off,
+                             c->tile_nown, c->stream);
+      });
+    } else {
+      s = launch(c, LBM_KC_FUSED, "k_march", [&] {
+        ls = launch_fused<T>(c->g, c->ph, fin, fout, Pin, Pout, c->flags, c->num_sms, c->stream);
+      });
+    }
     if (ls) return fail(c, ls, "fused kernel launch rejected");
     if (s) return s;
     c->cur ^= 1;
@@ -204,6 +221,7 @@ template <typename T>
 lbm_status do_step(lbm_ctx* c, int nsteps) {
   if constexpr (sizeof(T) >= 4) {  // the single-pass kernel stores 4- and 8-byte populations only
     if (c->prm.kernel == LBM_KERNEL_FUSED && fused_supported<T>(c->g, c->ph)) return step_fused<T>(c, nsteps);
+    if (c->prm.kernel == LBM_KERNEL_TILED && c->n_tiles > 0) return step_fused<T>(c, nsteps);
   }
   return step_two_pass<T>(c, nsteps);
 }
@@ -261,7 +279,7 @@ bool valid_params(const lbm_params* p) {
   if (p->nx < 4 || p->ny < 4) return false;
   if (!(p->tau[0] > 0.5) || !(p->tau[1] > 0.5)) return false;
   if (p->storage < LBM_STORE_FP32 || p->storage > LBM_STORE_BF16) return false;
-  if (p->kernel < LBM_KERNEL_AUTO || p->kernel > LBM_KERNEL_FUSED) return false;
+  if (p->kernel < LBM_KERNEL_AUTO || p->kernel > LBM_KERNEL_TILED) return false;
   if (p->max_interface < 0) return false;
   return true;
 }
@@ -327,6 +345,10 @@ lbm_status lbm_create(const lbm_params* params, void* d_workspace, size_t bytes,
   c->iface_list = (int*)(c->ws + L.list);
   c->iface_mask = (uint32_t*)(c->ws + L.imask);
   c->fluid_list = (int*)(c->ws + L.flist);
+  c->n_tiles = uses_tiles(params) ? tile_count(g) : 0;
+  c->tile_entries = c->n_tiles ? (uint16_t*)(c->ws + L.tent) : nullptr;
+  c->tile_off = c->n_tiles ? (int*)(c->ws + L.toff) : nullptr;
+  c->tile_nown = c->n_tiles ? (int*)(c->ws + L.tnown) : nullptr;
   c->scan_counts = (int*)(c->ws + L.counts);
   c->small = (int*)(c->ws + L.small);
   c->partial = (double*)(c->ws + L.partial);
@@ -408,6 +430,19 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* d_mask) {
     k_iface_mask<<<(c->n_iface + 127) / 128, 128, 0, c->stream>>>(c->flags, c->iface_list, c->n_iface, g,
                                                                   c->iface_mask);
     if ((s = after_launch(c, "k_iface_mask"))) return s;
+  }
+  if (c->n_tiles > 0) {
+    // per-tile lists of the tiled schedule: counts, offsets (fixed-order
+    // scan, total at tile_off[n_tiles]), entries
+    const int ntx = (g.nx + TILE_W - 1) / TILE_W;
+    const int nt = (int)c->n_tiles;
+    k_tile_lists<<<nt, TILE_LIST_THREADS, 0, c->stream>>>(c->flags, g, ntx, nullptr, c->tile_off, c->tile_nown, nullptr);
+    if ((s = after_launch(c, "k_tile_lists(count)"))) return s;
+    k_iface_scan<<<1, 1024, 0, c->stream>>>(c->tile_off, nt, c->tile_off + nt);
+    if ((s = after_launch(c, "k_iface_scan(tiles)"))) return s;
+    k_tile_lists<<<nt, TILE_LIST_THREADS, 0, c->stream>>>(c->flags, g, ntx, c->tile_off, nullptr, nullptr,
+                                                     c->tile_entries);
+    if ((s = after_launch(c, "k_tile_lists(write)"))) return s;
   }
   c->has_geometry = true;
   return LBM_OK;

@@ -6,6 +6,7 @@
 #include "lbm_fused.cuh"
 #include "lbm_geometry.cuh"
 #include "lbm_kernels.cuh"
+#include "lbm_tiled.cuh"
 
 using lbm::Geo;
 using lbm::Phys;
@@ -31,6 +32,10 @@ struct lbm_ctx {
   int* iface_list;
   uint32_t* iface_mask; // fluid neighbours of each interface-solid cell (5 x 5 stencil bits)
   int* fluid_list;     // fluid nodes in node order, edge nodes tagged (padded indices)
+  uint16_t* tile_entries; // tiled schedule: per-tile lists of region slots (null if unused)
+  int* tile_off;       // tiled schedule: first entry of each tile, total at [ntiles]
+  int* tile_nown;      // tiled schedule: owned fluid nodes of each tile
+  int64_t n_tiles;
   int* scan_counts;    // per-block interface counts / offsets
   int* small;          // [0] error count, [1] interface total, [2] fluid total
   double* partial;     // mass partial sums

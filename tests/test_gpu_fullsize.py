@@ -13,7 +13,7 @@ interior.
 
 Tolerances. FP32: the GPU's step rounds each result a few times in FP32 on
 values below 0.5 (one FP32 unit at 0.5 is 6e-8): 1e-6 (also for the
-single-pass schedule). FP16: the stored deviation from w_i rho_ref is
+single-pass schedules). FP16: the stored deviation from w_i rho_ref is
 rounded to 11 significant bits, at most 2^-11 x 0.5 = 2.4e-4 for |f| < 0.5,
 plus the FP32 term: 2.5e-4. BF16: 8 significant bits, 2^-8 x 0.5 = 2.0e-3:
 2.5e-3."""
@@ -63,7 +63,8 @@ def _windows(mask, rA, count=4, seed=7):
 
 
 @pytest.mark.parametrize("storage,kernel,tol", [("fp32", "auto", 1e-6), ("fp16", "auto", 2.5e-4),
-                                                ("bf16", "auto", 2.5e-3), ("fp32", "fused", 1e-6)])
+                                                ("bf16", "auto", 2.5e-3), ("fp32", "fused", 1e-6),
+                                                ("fp32", "tiled", 1e-6)])
 def test_full_size_step_matches_oracle_on_windows(workload, storage, kernel, tol):
     mask, rA, rB = workload
     wins = _windows(mask, rA)

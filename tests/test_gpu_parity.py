@@ -22,7 +22,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 from paper_2009_12584_gb300 import lbm  # noqa: E402
 
-KERNELS = ["two_pass", "fused"]
+KERNELS = ["two_pass", "fused", "tiled"]
 
 WETTINGS = {
     "mc": (dict(bc=oracle.BC_MARTYS_CHEN, G_s=(-0.2, 0.2)), ("martys_chen", dict(G_s=(-0.2, 0.2)))),
@@ -197,10 +197,11 @@ def test_checkpoint_restore_is_exact():
 @pytest.mark.parametrize("storage", ["fp32", "fp64"])
 @pytest.mark.parametrize("wet", ["mc", "llkc_self", "improved", "improved_self_d2q9", "constant"])
 @pytest.mark.parametrize("case", ["porous_periodic", "wall_walled"])
-def test_fused_matches_two_pass_bitwise(storage, wet, case):
-    """Both schedules run the same node arithmetic and the same density sums
+def test_single_pass_matches_two_pass_bitwise(storage, wet, case):
+    """The schedules run the same node arithmetic and the same density sums
     in the same order, so they must agree bit for bit (several 30-column
-    strips of the single-pass kernel plus a ragged one, row segments)."""
+    strips of the marching kernel plus a ragged one, row segments; several
+    32 x 16 tiles of the tiled kernel plus ragged ones in x and y)."""
     if case == "porous_periodic":
         nx, ny, per = 157, 131, (True, True)
         mask = inputs.porous_disks(nx, ny, 0.35, rmin=3, rmax=9, seed=5)
@@ -215,10 +216,11 @@ def test_fused_matches_two_pass_bitwise(storage, wet, case):
         s = lbm.Simulation(nx, ny, periodic_x=per[0], periodic_y=per[1], storage=storage, kernel=kernel)
         s.set_geometry(mask).set_wetting(kind, **gkw).init_fields(rA, rB).step(37)
         outs.append((s.populations(), s.moments(), s.mass()))
-    assert torch.equal(outs[0][0], outs[1][0])
-    for a, b in zip(outs[0][1], outs[1][1]):
-        assert torch.equal(a, b)
-    assert np.array_equal(outs[0][2], outs[1][2])
+    for other in outs[1:]:
+        assert torch.equal(outs[0][0], other[0])
+        for a, b in zip(outs[0][1], other[1]):
+            assert torch.equal(a, b)
+        assert np.array_equal(outs[0][2], other[2])
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
