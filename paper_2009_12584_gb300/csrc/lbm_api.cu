@@ -141,6 +141,7 @@ template <typename T>
 lbm_status step_two_pass(lbm_ctx* c, int nsteps) {
   using C = typename Pop<T>::C;
   const int nb = (c->n_fluid + 255) / 256;
+  const int nbc = (c->n_fluid + COLLIDE_THREADS - 1) / COLLIDE_THREADS;
   for (int t = 0; t < nsteps && c->n_fluid > 0; ++t) {
     const T* fin = (const T*)c->f[c->cur];
     T* fout = (T*)c->f[c->cur ^ 1];
@@ -159,8 +160,8 @@ lbm_status step_two_pass(lbm_ctx* c, int nsteps) {
       if (s) return s;
     }
     s = launch(c, LBM_KC_COLLIDE, "k_collide_list", [&] {
-      k_collide_list<T><<<nb, 256, 0, c->stream>>>(fin, fout, P, Pref, c->flags, c->fluid_list, c->n_fluid, c->g,
-                                                  kphys<C>(c->ph));
+      k_collide_list<T><<<nbc, COLLIDE_THREADS, 0, c->stream>>>(fin, fout, P, Pref, c->flags, c->fluid_list,
+                                                                c->n_fluid, c->g, kphys<C>(c->ph));
     });
     if (s) return s;
     c->cur ^= 1;

@@ -191,6 +191,10 @@ __device__ __forceinline__ void collide_node_pair(const T* __restrict__ f, T* __
 }
 
 // ---- K3 over the fluid-node list ------------------------------------------
+// 128-thread CTAs, 8 per SM at 64 registers: a CTA's slot frees sooner than
+// with 256 threads when its warps finish at different times.
+constexpr int COLLIDE_THREADS = 128;
+
 // Three paths, chosen per warp so that a warp never splits between them: a
 // warp whose 32 nodes are all bulk (eight fluid neighbours, away from
 // periodic borders) loads no flags and has no adhesion and no bounce-back;
@@ -251,7 +255,7 @@ __device__ __forceinline__ void collide_node(const T* __restrict__ f, T* __restr
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_collide_list(const T* __restrict__ f, T* __restrict__ fo,
+__global__ void __launch_bounds__(COLLIDE_THREADS, 8) k_collide_list(const T* __restrict__ f, T* __restrict__ fo,
                                                          const typename Pop<T>::C* __restrict__ P,
                                                          const typename Pop<T>::C* __restrict__ Pref,
                                                          const uint16_t* __restrict__ flags,
