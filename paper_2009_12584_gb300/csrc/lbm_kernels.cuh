@@ -22,6 +22,18 @@ __device__ __forceinline__ void gather(const T* __restrict__ f, const Geo& g, in
     Pop<T>::ld2(f, pslot(g, i, k - cx_of(i) - cy_of(i) * g.px), ref[0][i], ref[1][i], out[0][i], out[1][i]);
 }
 
+// The list entry is the first load of every node and the pulls depend on
+// it. A CTA asks L2 for the list lines of the CTA LIST_AHEAD launches after
+// it (one 128-byte line per 32 entries), so that CTA finds them there.
+constexpr int LIST_AHEAD = 1024;
+template <int NT>
+__device__ __forceinline__ void prefetch_list_ahead(const int* __restrict__ list, int n) {
+  if (threadIdx.x < NT / 32) {
+    const int64_t t = ((int64_t)blockIdx.x + LIST_AHEAD) * NT + threadIdx.x * 32;
+    if (t < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(list + t));
+  }
+}
+
 // Encoding references of 16-bit storage. A 2-byte population is stored as
 // its deviation from w_i rho of the node that wrote it, rho being that
 // node's density when it collided (kept in the reference density plane
@@ -261,6 +273,7 @@ __global__ void __launch_bounds__(COLLIDE_THREADS, 8) k_collide_list(const T* __
                                                          const uint16_t* __restrict__ flags,
                                                          const int* __restrict__ list, int nfluid, Geo g,
                                                          PhysK<typename Pop<T>::C> ph) {
+  prefetch_list_ahead<COLLIDE_THREADS>(list, nfluid);
   collide_node<T>(f, fo, P, Pref, flags, list, blockIdx.x * blockDim.x + threadIdx.x, nfluid, g, ph);
 }
 
