@@ -440,9 +440,11 @@ __global__ void k_get_populations(const T* __restrict__ f, const typename Pop<T>
 }
 
 // Wrapped compact index of (x, y) for caller arrays [ny][nx].
+// Compact index of node (x, y) with x in [-1, nx] and y in [-1, ny],
+// wrapped once (a D2Q9 neighbour of an owned node).
 __device__ __forceinline__ int64_t wrap_compact(const Geo& g, int x, int y) {
-  x = (x + g.nx) % g.nx;
-  y = (y + g.ny) % g.ny;
+  x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
+  y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
   return (int64_t)y * g.nx + x;
 }
 
@@ -466,23 +468,37 @@ __global__ void k_set_state(T* __restrict__ f, typename Pop<T>::C* __restrict__ 
   const uint16_t fl = flags[k];
   if (fl & F_SOLID) return;
   const int64_t N = (int64_t)g.nx * g.ny;
-  // O at node m, component s, direction j
-  // evaluated in the compute type: FP32 for 4- and 2-byte storage (FP64
-  // arithmetic is a small fraction of the FP32 rate on this GPU), FP64 for
-  // FP64 storage
-  auto O = [&](int64_t m, int s, int j) -> C {
-    if (SRC == 0) return C(fin[(s * 9 + j) * N + m]);
-    const C r = C(s ? rB[m] : rA[m]);
-    const C vx = ux ? C(ux[m]) : C(0), vy = uy ? C(uy[m]) : C(0);
-    const C cu = C(cx_of(j)) * vx + C(cy_of(j)) * vy;
-    return r * w_of<C>(j) * (C(1) + C(3) * cu + C(4.5) * cu * cu - C(1.5) * (vx * vx + vy * vy));
+  // Eq. 2 is evaluated in the compute type: FP32 for 4- and 2-byte storage,
+  // FP64 for FP64 storage. The caller's FP64 fields of a node are converted
+  // once (FP64 instructions, conversions included, run at a small fraction
+  // of the FP32 rate on this GPU).
+  struct Node { C r[2], vx, vy; };
+  auto node = [&](int64_t m) {
+    Node v;
+    v.r[0] = C(rA[m]);
+    v.r[1] = C(rB[m]);
+    v.vx = ux ? C(ux[m]) : C(0);
+    v.vy = uy ? C(uy[m]) : C(0);
+    return v;
+  };
+  auto feq = [&](const Node& v, int s, int j) -> C {
+    const C cu = C(cx_of(j)) * v.vx + C(cy_of(j)) * v.vy;
+    return v.r[s] * w_of<C>(j) * (C(1) + C(3) * cu + C(4.5) * cu * cu - C(1.5) * (v.vx * v.vx + v.vy * v.vy));
   };
   const int64_t n = (int64_t)y * g.nx + x;
+  Node own{};
+  if (SRC == 1) own = node(n);
+  // O at node m (whose converted fields are v when SRC == 1), component s,
+  // direction j
+  auto O = [&](int64_t m, const Node& v, int s, int j) -> C {
+    if (SRC == 0) return C(fin[(s * 9 + j) * N + m]);
+    return feq(v, s, j);
+  };
   C rho0[2];
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     C r = C(0);
-    for (int j = 0; j < 9; ++j) r += O(n, s, j);
+    for (int j = 0; j < 9; ++j) r += O(n, own, s, j);
     rho0[s] = r;
   }
   stP_ghosts(Pref, g, x, y, rho0[0], rho0[1]);
@@ -490,12 +506,14 @@ __global__ void k_set_state(T* __restrict__ f, typename Pop<T>::C* __restrict__ 
   write_refs<T>(rho0, ref);
   C fv[2][9];
 #pragma unroll
-  for (int s = 0; s < 2; ++s)
+  for (int j = 0; j < 9; ++j) {
+    const bool bounce = (j != 0) && (fl & nb_bit(j));
+    const int64_t m = bounce ? n : wrap_compact(g, x + cx_of(j), y + cy_of(j));
+    Node nb{};
+    if (SRC == 1 && !bounce) nb = node(m);
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
-      const bool bounce = (j != 0) && (fl & nb_bit(j));
-      fv[s][j] = C(bounce ? O(n, s, opp_of(j)) : O(wrap_compact(g, x + cx_of(j), y + cy_of(j)), s, j));
-    }
+    for (int s = 0; s < 2; ++s) fv[s][j] = C(bounce ? O(n, own, s, opp_of(j)) : O(m, nb, s, j));
+  }
   store_node(f, g, x, y, k, fv, ref);
   // the bounced slots: store_bounced writes fv[s][opp(i)] into slot i, so
   // pass it the received values O_i(x) in the opposite slots
@@ -504,7 +522,7 @@ __global__ void k_set_state(T* __restrict__ f, typename Pop<T>::C* __restrict__ 
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
-      for (int i = 0; i < 9; ++i) rv[s][opp_of(i)] = C(O(n, s, i));
+      for (int i = 0; i < 9; ++i) rv[s][opp_of(i)] = C(O(n, own, s, i));
     store_bounced(f, g, x, y, fl, rv, ref);
   }
 }
