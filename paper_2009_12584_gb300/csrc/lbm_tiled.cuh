@@ -196,12 +196,6 @@ constexpr size_t tile_smem() {
   return (size_t)9 * TILE_RS * sizeof(typename CPair<typename Pop<T>::C>::V);
 }
 
-// The tiled kernel keeps 4- and 8-byte populations only, like k_march.
-template <typename T>
-inline bool tiled_supported() {
-  return sizeof(T) >= 4;
-}
-
 template <typename T>
 inline lbm_status launch_tiled(const Geo& g, const Phys& ph, const T* fin, T* fout, const typename Pop<T>::C* P,
                                typename Pop<T>::C* Po, const uint16_t* flags, const uint16_t* entries,
