@@ -71,6 +71,14 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+def effective_schedule(kernel, storage):
+    """The schedule lbm_step runs: 16-bit storage always takes the two-pass
+    one; AUTO takes the tiled one for 4- and 8-byte storage."""
+    if storage in ("fp16", "bf16"):
+        return "two_pass"
+    return "tiled" if kernel == "auto" else kernel
+
+
 def measured_traffic(kernel_class, storage):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
@@ -420,7 +428,10 @@ def main():
     alg_bytes = bpu * nf
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
     pk, pk_kind = peaks()
-    traffic = measured_traffic(dom, args.storage)
+    # the single-pass class is k_tile under AUTO and TILED (4- and 8-byte
+    # storage), k_march under FUSED
+    tkey = dom if dom != "fused" else ("tile" if effective_schedule(args.kernel, args.storage) == "tiled" else "march")
+    traffic = measured_traffic(tkey, args.storage)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
                 "peak_kind": pk_kind, "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
                 "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
@@ -476,6 +487,7 @@ def main():
                            "nx": n, "ny": n, "fluid_nodes": nf, "solid_fraction": round(1 - nf / n / n, 4),
                            "bc": "virtual_avg", "xi": XI, "chi": chi, "tau": 1.0, "G_AB": 3.0,
                            "storage": args.storage, "kernel": args.kernel,
+                           "schedule": effective_schedule(args.kernel, args.storage),
                            "l2": "inputs larger than L2 (populations %.1f GB per buffer)"
                                  % (18 * n * n * BYTES_PER_UPDATE[args.storage] / 144 * 4 / 1e9),
                            "all_node_mlups": round(world * n * n * args.steps / (t_ms / 1e3) / 1e6, 1),

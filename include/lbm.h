@@ -89,11 +89,12 @@ typedef enum {
  * tile, each a compacted list of its fluid nodes plus the one-node ring
  * around it (computed again), built by lbm_set_geometry (workspace grows by
  * 2 bytes per ring-extended region slot, about 2.5 bytes per node, for 4-
- * and 8-byte storage). FUSED and TILED keep 4- and 8-byte populations only;
+ * and 8-byte storage, under TILED or AUTO). FUSED and TILED keep 4- and 8-byte populations only;
  * FP16/BF16 storage runs TWO_PASS under any choice. All schedules give the
  * same results bit for bit. AUTO picks the schedule measured fastest on
- * GB300 under the library's default settings (currently TWO_PASS; TILED
- * moves 30% fewer bytes but ties with it in time). */
+ * GB300: TILED for 4- and 8-byte storage (it moves 30% fewer bytes than
+ * TWO_PASS and is 4% faster on the 8192^2 porous medium; its lists are then
+ * built by lbm_set_geometry as for TILED), TWO_PASS for 16-bit storage. */
 typedef enum {
   LBM_KERNEL_AUTO = 0,
   LBM_KERNEL_TWO_PASS = 1,

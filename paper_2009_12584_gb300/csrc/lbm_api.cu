@@ -43,9 +43,11 @@ struct Layout {
       total;
 };
 
-// Whether a context keeps the per-tile lists of the tiled schedule.
+// Whether a context keeps the per-tile lists of the tiled schedule (the
+// schedule AUTO picks for 4- and 8-byte storage).
 bool uses_tiles(const lbm_params* p) {
-  return p->kernel == LBM_KERNEL_TILED && (p->storage == LBM_STORE_FP32 || p->storage == LBM_STORE_FP64);
+  return (p->kernel == LBM_KERNEL_TILED || p->kernel == LBM_KERNEL_AUTO) &&
+         (p->storage == LBM_STORE_FP32 || p->storage == LBM_STORE_FP64);
 }
 
 constexpr int MASS_BLOCKS = 1024;
@@ -222,7 +224,8 @@ template <typename T>
 lbm_status do_step(lbm_ctx* c, int nsteps) {
   if constexpr (sizeof(T) >= 4) {  // the single-pass kernel stores 4- and 8-byte populations only
     if (c->prm.kernel == LBM_KERNEL_FUSED && fused_supported<T>(c->g, c->ph)) return step_fused<T>(c, nsteps);
-    if (c->prm.kernel == LBM_KERNEL_TILED && c->n_tiles > 0) return step_fused<T>(c, nsteps);
+    const bool tiled = c->prm.kernel == LBM_KERNEL_TILED || c->prm.kernel == LBM_KERNEL_AUTO;
+    if (tiled && c->n_tiles > 0) return step_fused<T>(c, nsteps);
   }
   return step_two_pass<T>(c, nsteps);
 }

@@ -112,6 +112,14 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
   const int n_own = nown[tile];
   if (n_own == 0) return;  // the whole CTA: nothing owned, nothing to store
   const int e0 = offsets[tile], n_all = offsets[tile + 1] - e0;
+  // The entries are the first load of every node and its pulls depend on
+  // them: ask L2 for the entries of the tile LIST_AHEAD launches later (8
+  // lines of 64 entries cover a region).
+  static_assert(8 * 64 >= TILE_RS, "eight 128-byte lines hold a tile's entries");
+  if (threadIdx.x < 8 && tile + LIST_AHEAD < (int)gridDim.x) {
+    const int e1 = __ldg(offsets + tile + LIST_AHEAD);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(entries + e1 + threadIdx.x * 64));
+  }
   const int x0 = (tile % ntx) * TILE_W, y0 = (tile / ntx) * TILE_H;
   const int korg = g.idx(x0 - 1, y0 - 1);  // padded index of slot 0
   C ref[2][9];  // storage references: unused for 4- and 8-byte populations

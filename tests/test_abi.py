@@ -121,8 +121,11 @@ def test_tiled_schedule_workspace_without_gpu():
             base = lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="two_pass"))
             tiled = lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="tiled"))
             assert tiled - base == extra, (nx, ny, st)
+            # AUTO runs the tiled schedule for 4- and 8-byte storage
+            assert lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="auto")) == tiled
         for st in ("fp16", "bf16"):  # 16-bit storage runs the two-pass schedule
-            assert (lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="tiled"))
-                    == lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="two_pass")))
+            for k in ("tiled", "auto"):
+                assert (lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel=k))
+                        == lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="two_pass")))
     with pytest.raises(lbm.LbmError):
         lbm.workspace_bytes(lbm.make_params(8, 8, kernel=4))
