@@ -79,16 +79,26 @@ def effective_schedule(kernel, storage):
     return "tiled" if kernel == "auto" else kernel
 
 
-def measured_traffic(kernel_class, storage):
+def l2_fetch_for(kernel, storage, requested):
+    """The L2 fetch granularity an arm runs with: the one requested, else the
+    one each schedule runs best with (the tiled kernel's scattered ring reads
+    gain from 128-byte fetches, the two-pass pulls from 32-byte ones)."""
+    if requested >= 0:
+        return requested
+    return 128 if effective_schedule(kernel, storage) == "tiled" else 32
+
+
+def measured_traffic(kernel_class, storage, l2_fetch):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    on the current kernel sources with the same L2 fetch granularity (else
+    None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
     except (OSError, ValueError):
         return None
     e = d.get(f"{kernel_class}/{storage}")
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash() or e.get("l2_fetch_granularity_bytes") != l2_fetch:
         return None
     return e.get("bytes_per_launch_full")
 
@@ -234,10 +244,11 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_single(n, mask, rA, rB, nf, storage, kernel, steps, warmup):
+def run_single(n, mask, rA, rB, nf, storage, kernel, steps, warmup, l2_fetch):
     """The throughput workload with another population storage."""
     import torch
     from paper_2009_12584_gb300 import lbm
+    l2_prev = lbm.set_l2_fetch_granularity(l2_fetch) if l2_fetch else None
     sim = lbm.Simulation(n, n, periodic_x=True, periodic_y=True, storage=storage, kernel=kernel)
     sim.set_geometry(mask).set_wetting("virtual_avg", G_s=(3.0, 3.0), chi=chi_from_xi(XI)).init_fields(rA, rB)
     sim.step(warmup)
@@ -257,9 +268,12 @@ def run_single(n, mask, rA, rB, nf, storage, kernel, steps, warmup):
     out = {"value": round(nf * steps / (t_ms / 1e3) / 1e6, 1), "unit": "MLUPS", "ms_per_step": round(t_ms / steps, 4),
            "roofline": {"kernel": dom, "achieved": round(ach, 1), "frac": round(ach / pk["hbm_gbs"], 4),
                         "algorithmic_bytes_per_update": bpu},
-           "kernel_ms_per_step": {k: round(v / steps, 4) for k, v in ms_cls.items() if cnt_cls[k]}}
+           "kernel_ms_per_step": {k: round(v / steps, 4) for k, v in ms_cls.items() if cnt_cls[k]},
+           "l2_fetch_granularity_bytes": l2_fetch}
     del sim
     torch.cuda.empty_cache()
+    if l2_prev is not None:
+        lbm.set_l2_fetch_granularity(l2_prev)
     return out
 
 
@@ -368,8 +382,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the fp16/bf16, batched and accuracy arms")
-    ap.add_argument("--l2-fetch", type=int, default=32, choices=[0, 32, 64, 128],
-                    help="L2 fetch granularity hint for this process (0: leave the CUDA default)")
+    ap.add_argument("--l2-fetch", type=int, default=-1, choices=[-1, 0, 32, 64, 128],
+                    help="L2 fetch granularity hint for this process (0: leave the CUDA default; "
+                         "-1: per schedule, 128 bytes for the tiled one and 32 for the two-pass one)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -388,7 +403,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
-    l2_prev = lbm.set_l2_fetch_granularity(args.l2_fetch) if args.l2_fetch else None
+    l2_fetch = l2_fetch_for(args.kernel, args.storage, args.l2_fetch)
+    l2_prev = lbm.set_l2_fetch_granularity(l2_fetch) if l2_fetch else None
 
     n = args.n
     mask, rA, rB = workload(n)
@@ -431,7 +447,7 @@ def main():
     # the single-pass class is k_tile under AUTO and TILED (4- and 8-byte
     # storage), k_march under FUSED
     tkey = dom if dom != "fused" else ("tile" if effective_schedule(args.kernel, args.storage) == "tiled" else "march")
-    traffic = measured_traffic(tkey, args.storage)
+    traffic = measured_traffic(tkey, args.storage, l2_fetch)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
                 "peak_kind": pk_kind, "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
                 "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
@@ -471,7 +487,8 @@ def main():
         del sim
         torch.cuda.empty_cache()
         for st in ("fp16", "bf16"):
-            extra[st] = run_single(n, mask, rA, rB, nf, st, args.kernel, args.steps, args.warmup)
+            extra[st] = run_single(n, mask, rA, rB, nf, st, args.kernel, args.steps, args.warmup,
+                                   l2_fetch_for(args.kernel, st, args.l2_fetch))
         for st in ("fp32", "fp16"):
             extra[f"batched_{st}"] = run_batched(st, args.steps, args.warmup)
         extra["err_vs_fp64"] = accuracy()
@@ -492,7 +509,7 @@ def main():
                                  % (18 * n * n * BYTES_PER_UPDATE[args.storage] / 144 * 4 / 1e9),
                            "all_node_mlups": round(world * n * n * args.steps / (t_ms / 1e3) / 1e6, 1),
                            "parallelism": f"replicas x{world}",
-                           "l2_fetch_granularity_bytes": args.l2_fetch or l2_prev},
+                           "l2_fetch_granularity_bytes": l2_fetch or l2_prev},
                 "roofline": roofline, "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu, **extra}
         print(json.dumps(line), flush=True)

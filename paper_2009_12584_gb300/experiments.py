@@ -358,7 +358,8 @@ def main(argv=None):
     cu.add_argument("--steps", type=int, default=100000)
     cu.add_argument("--sample-every", type=int, default=100)
     args = ap.parse_args(argv)
-    lbm.set_l2_fetch_granularity(32)  # fastest for the step (lbm_set_l2_fetch_granularity)
+    # 128-byte L2 fetches: fastest for the tiled schedule (FP32 single runs) and the batched one
+    lbm.set_l2_fetch_granularity(128)
     if args.cmd in ("curvature", "viscosity"):
         res = (curvature_study(t_end=args.t_end, storage=args.storage) if args.cmd == "curvature"
                else viscosity_study(t_end=args.t_end, storage=args.storage))
