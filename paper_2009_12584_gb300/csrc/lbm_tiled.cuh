@@ -28,11 +28,12 @@
 
 namespace lbm {
 
-constexpr int TILE_W = 32, TILE_H = 12;     // owned nodes per tile
+constexpr int TILE_W = 32, TILE_H = 14;     // owned nodes per tile
 constexpr int TILE_RW = TILE_W + 2;         // region pitch (one ring node each side)
 constexpr int TILE_RH = TILE_H + 2;
 constexpr int TILE_RS = TILE_RW * TILE_RH;  // region slots
 constexpr int TILE_THREADS = 256;           // k_tile
+constexpr int TILE_AHEAD = 512;             // tiles between a CTA and the one whose entries it prefetches
 constexpr int TILE_LIST_THREADS = 256;      // k_tile_lists
 static_assert(TILE_RS <= 2048, "slots must fit the 11 slot bits of an entry");
 
@@ -113,11 +114,12 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
   if (n_own == 0) return;  // the whole CTA: nothing owned, nothing to store
   const int e0 = offsets[tile], n_all = offsets[tile + 1] - e0;
   // The entries are the first load of every node and its pulls depend on
-  // them: ask L2 for the entries of the tile LIST_AHEAD launches later (8
-  // lines of 64 entries cover a region).
-  static_assert(8 * 64 >= TILE_RS, "eight 128-byte lines hold a tile's entries");
-  if (threadIdx.x < 8 && tile + LIST_AHEAD < (int)gridDim.x) {
-    const int e1 = __ldg(offsets + tile + LIST_AHEAD);
+  // them: ask L2 for the entries of the tile TILE_AHEAD launches later (one
+  // 128-byte line per 64 entries, enough lines for a full region).
+  constexpr int ENTRY_LINES = (TILE_RS + 63) / 64;
+  static_assert(ENTRY_LINES <= TILE_THREADS, "one thread per line");
+  if (threadIdx.x < ENTRY_LINES && tile + TILE_AHEAD < (int)gridDim.x) {
+    const int e1 = __ldg(offsets + tile + TILE_AHEAD);
     asm volatile("prefetch.global.L2 [%0];" ::"l"(entries + e1 + threadIdx.x * 64));
   }
   const int x0 = (tile % ntx) * TILE_W, y0 = (tile / ntx) * TILE_H;

@@ -109,14 +109,14 @@ def test_argument_checks_before_any_cuda_call(lib):
 
 def test_tiled_schedule_workspace_without_gpu():
     """The tiled schedule adds its per-tile lists (2 bytes per region slot of
-    each 32 x 12 tile plus per-tile offsets and counts, each array 256-byte
+    each 32 x 14 tile plus per-tile offsets and counts, each array 256-byte
     aligned) for 4- and 8-byte
     storage only; an unknown schedule is rejected."""
     lbm.load()
     align = lambda n: (n + 255) // 256 * 256
     for nx, ny in ((8192, 8192), (100, 70), (4, 4)):
-        nt = -(-nx // 32) * -(-ny // 12)
-        extra = align(nt * 34 * 14 * 2) + align((nt + 1) * 4) + align(nt * 4)
+        nt = -(-nx // 32) * -(-ny // 14)
+        extra = align(nt * 34 * 16 * 2) + align((nt + 1) * 4) + align(nt * 4)
         for st in ("fp32", "fp64"):
             base = lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="two_pass"))
             tiled = lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="tiled"))

@@ -201,7 +201,7 @@ def test_single_pass_matches_two_pass_bitwise(storage, wet, case):
     """The schedules run the same node arithmetic and the same density sums
     in the same order, so they must agree bit for bit (several 30-column
     strips of the marching kernel plus a ragged one, row segments; several
-    32 x 16 tiles of the tiled kernel plus ragged ones in x and y)."""
+    32 x 14 tiles of the tiled kernel plus ragged ones in x and y)."""
     if case == "porous_periodic":
         nx, ny, per = 157, 131, (True, True)
         mask = inputs.porous_disks(nx, ny, 0.35, rmin=3, rmax=9, seed=5)
