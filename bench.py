@@ -72,10 +72,11 @@ def source_hash():
 
 
 def effective_schedule(kernel, storage):
-    """The schedule lbm_step runs: 16-bit storage always takes the two-pass
-    one; AUTO takes the tiled one for 4- and 8-byte storage."""
+    """The schedule lbm_step runs: AUTO takes the tiled one for 4- and 8-byte
+    storage and the two-pass one for 16-bit storage; 16-bit storage runs a
+    FUSED choice as two-pass too (the marching kernel has no 16-bit path)."""
     if storage in ("fp16", "bf16"):
-        return "two_pass"
+        return "tiled" if kernel == "tiled" else "two_pass"
     return "tiled" if kernel == "auto" else kernel
 
 

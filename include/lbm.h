@@ -81,20 +81,23 @@ typedef enum {
   LBM_STORE_BF16 = 3
 } lbm_storage;
 
-/* Kernel schedule for lbm_step. TWO_PASS: a density pass, the virtual
- * density pass, then one fused force+collide+stream pull kernel. FUSED: one
- * kernel per step that also writes the densities of the next step (the
- * density plane is double-buffered), warps marching up column strips.
- * TILED: the same single-pass contract on 32 x 14 tiles, one CTA per
- * tile, each a compacted list of its fluid nodes plus the one-node ring
- * around it (computed again), built by lbm_set_geometry (workspace grows by
- * 2 bytes per ring-extended region slot, about 2.5 bytes per node, for 4-
- * and 8-byte storage, under TILED or AUTO). FUSED and TILED keep 4- and 8-byte populations only;
- * FP16/BF16 storage runs TWO_PASS under any choice. All schedules give the
- * same results bit for bit. AUTO picks the schedule measured fastest on
- * GB300: TILED for 4- and 8-byte storage (it moves a quarter fewer bytes than
- * TWO_PASS and is 8% faster on the 8192^2 porous medium; its lists are then
- * built by lbm_set_geometry as for TILED), TWO_PASS for 16-bit storage. */
+/* Kernel schedule for lbm_step. All schedules give the same results bit for
+ * bit.
+ * TWO_PASS: a density pass, the virtual density pass, then one fused
+ *   force+collide+stream pull kernel.
+ * FUSED: one kernel per step that also writes the densities of the next
+ *   step (the density plane is double-buffered), warps marching up column
+ *   strips; 4- and 8-byte storage only (16-bit storage runs TWO_PASS).
+ * TILED: the same single-pass contract on 32 x 14 tiles, one CTA per tile,
+ *   each a compacted list of its fluid nodes plus the one-node ring around
+ *   it (computed again), built by lbm_set_geometry: the workspace grows by 2
+ *   bytes per ring-extended region slot (about 2.4 bytes per node), and for
+ *   16-bit storage by a third density plane (8 bytes per padded node), since
+ *   a 16-bit step decodes with the densities of the step before.
+ * AUTO picks the schedule measured fastest on GB300: TILED for 4- and 8-byte
+ * storage (a quarter fewer bytes than TWO_PASS and 8% faster on the 8192^2
+ * porous medium; its lists are then built as for TILED), TWO_PASS for 16-bit
+ * storage. */
 typedef enum {
   LBM_KERNEL_AUTO = 0,
   LBM_KERNEL_TWO_PASS = 1,

@@ -44,10 +44,17 @@ struct Layout {
 };
 
 // Whether a context keeps the per-tile lists of the tiled schedule (the
-// schedule AUTO picks for 4- and 8-byte storage).
+// schedule AUTO picks for 4- and 8-byte storage; 16-bit storage runs it
+// only when asked for).
 bool uses_tiles(const lbm_params* p) {
-  return (p->kernel == LBM_KERNEL_TILED || p->kernel == LBM_KERNEL_AUTO) &&
-         (p->storage == LBM_STORE_FP32 || p->storage == LBM_STORE_FP64);
+  const bool wide = p->storage == LBM_STORE_FP32 || p->storage == LBM_STORE_FP64;
+  return p->kernel == LBM_KERNEL_TILED || (p->kernel == LBM_KERNEL_AUTO && wide);
+}
+
+// The tiled schedule with 16-bit storage keeps a third density plane: a step
+// reads the encoding references rho(t - 1) and rho(t) and writes rho(t + 1).
+bool tiled16(const lbm_params* p) {
+  return p->kernel == LBM_KERNEL_TILED && (p->storage == LBM_STORE_FP16 || p->storage == LBM_STORE_BF16);
 }
 
 constexpr int MASS_BLOCKS = 1024;
@@ -61,7 +68,7 @@ bool layout(const lbm_params* p, const Geo& g, Layout* L) {
   const int64_t scan_blocks = (N + SCAN_BLOCK - 1) / SCAN_BLOCK;
   size_t off = 0;
   L->f = off;        off = align_up(off + 2 * 18 * (size_t)g.plane * es, A);
-  L->P = off;        off = align_up(off + 4 * (size_t)g.plane * cs, A);
+  L->P = off;        off = align_up(off + (tiled16(p) ? 6 : 4) * (size_t)g.plane * cs, A);
   L->flags = off;    off = align_up(off + (size_t)g.plane * 2, A);
   L->list = off;     off = align_up(off + (size_t)cap * 4, A);
   L->imask = off;    off = align_up(off + (size_t)cap * 4, A);
@@ -203,7 +210,7 @@ lbm_status step_fused(lbm_ctx* c, int nsteps) {
     lbm_status ls = LBM_OK;
     if (c->n_tiles > 0) {
       s = launch(c, LBM_KC_FUSED, "k_tile", [&] {
-        ls = launch_tiled<T>(c->g, c->ph, fin, fout, Pin, Pout, c->flags, c->tile_entries, c->tile_off,
+        ls = launch_tiled<T>(c->g, c->ph, fin, fout, Pin, Pin, Pout, c->flags, c->tile_entries, c->tile_off,
                              c->tile_nown, c->stream);
       });
     } else {
@@ -220,12 +227,64 @@ lbm_status step_fused(lbm_ctx* c, int nsteps) {
   return LBM_OK;
 }
 
+// Tiled step with 16-bit storage. Between steps Pbuf[pcur] holds the
+// densities the current populations were encoded with (as for the two-pass
+// schedule) and, when p_valid, Pbuf[pcur ^ 1] the densities of the current
+// state. A step reads both and writes the next densities into Pbuf[2]; the
+// three pointers then rotate.
+template <typename T>
+lbm_status step_tiled16(lbm_ctx* c, int nsteps) {
+  using C = typename Pop<T>::C;
+  if (nsteps > 0 && !c->p_valid) {
+    lbm_status s = launch(c, LBM_KC_DENSITY, "k_density", [&] {
+      k_density<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>((const T*)c->f[c->cur], (C*)c->Pbuf[c->pcur ^ 1],
+                                                                  (const C*)c->Pbuf[c->pcur], c->flags, c->g,
+                                                                  kphys<C>(c->ph));
+    });
+    if (s) return s;
+    c->p_valid = true;
+  }
+  for (int t = 0; t < nsteps; ++t) {
+    const T* fin = (const T*)c->f[c->cur];
+    T* fout = (T*)c->f[c->cur ^ 1];
+    const C* Pref = (const C*)c->Pbuf[c->pcur];
+    C* P = (C*)c->Pbuf[c->pcur ^ 1];
+    C* Po = (C*)c->Pbuf[2];
+    lbm_status s;
+    if (c->ph.bc == BC_VAVG && c->n_iface > 0) {
+      s = launch(c, LBM_KC_VIRTUAL, "k_virtual_density", [&] {
+        k_virtual_density<C><<<(c->n_iface + 127) / 128, 128, 0, c->stream>>>(P, c->iface_mask, c->iface_list,
+                                                                               c->n_iface, c->g, kphys<C>(c->ph));
+      });
+      if (s) return s;
+    }
+    lbm_status ls = LBM_OK;
+    s = launch(c, LBM_KC_FUSED, "k_tile", [&] {
+      ls = launch_tiled<T>(c->g, c->ph, fin, fout, P, Pref, Po, c->flags, c->tile_entries, c->tile_off,
+                           c->tile_nown, c->stream);
+    });
+    if (ls) return fail(c, ls, "tiled kernel launch rejected");
+    if (s) return s;
+    c->cur ^= 1;
+    // the new populations were encoded with rho(t), their densities are
+    // rho(t + 1); the plane of rho(t - 1) is free
+    void* freed = c->Pbuf[c->pcur];
+    c->Pbuf[c->pcur] = c->Pbuf[c->pcur ^ 1];
+    c->Pbuf[c->pcur ^ 1] = c->Pbuf[2];
+    c->Pbuf[2] = freed;
+    c->P = c->Pbuf[c->pcur];
+  }
+  return LBM_OK;
+}
+
 template <typename T>
 lbm_status do_step(lbm_ctx* c, int nsteps) {
-  if constexpr (sizeof(T) >= 4) {  // the single-pass kernel stores 4- and 8-byte populations only
+  if constexpr (sizeof(T) >= 4) {  // the marching kernel stores 4- and 8-byte populations only
     if (c->prm.kernel == LBM_KERNEL_FUSED && fused_supported<T>(c->g, c->ph)) return step_fused<T>(c, nsteps);
     const bool tiled = c->prm.kernel == LBM_KERNEL_TILED || c->prm.kernel == LBM_KERNEL_AUTO;
     if (tiled && c->n_tiles > 0) return step_fused<T>(c, nsteps);
+  } else {
+    if (c->Pbuf[2] && c->n_tiles > 0) return step_tiled16<T>(c, nsteps);
   }
   return step_two_pass<T>(c, nsteps);
 }
@@ -342,6 +401,8 @@ lbm_status lbm_create(const lbm_params* params, void* d_workspace, size_t bytes,
   c->f[1] = c->ws + L.f + 18 * (size_t)g.plane * es;
   c->Pbuf[0] = c->ws + L.P;
   c->Pbuf[1] = c->ws + L.P + 2 * (size_t)g.plane * compute_size(params->storage);
+  c->Pbuf[2] = tiled16(params) ? c->ws + L.P + 4 * (size_t)g.plane * compute_size(params->storage) : nullptr;
+  c->Pbase = c->ws + L.P;
   c->pcur = 0;
   c->P = c->Pbuf[0];
   c->p_valid = false;
@@ -419,8 +480,8 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* d_mask) {
   }
   // clear the density planes so solid cells read as zero
   c->p_valid = false;
-  s = check_cuda(c, cudaMemsetAsync(c->Pbuf[0], 0, 4 * (size_t)g.plane * compute_size(c->prm.storage), c->stream),
-                 "cudaMemsetAsync");
+  s = check_cuda(c, cudaMemsetAsync(c->Pbase, 0, (c->Pbuf[2] ? 6 : 4) * (size_t)g.plane * compute_size(c->prm.storage),
+                                    c->stream), "cudaMemsetAsync");
   if (s) return s;
   int h[3];
   s = check_cuda(c, cudaMemcpyAsync(h, c->small, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");

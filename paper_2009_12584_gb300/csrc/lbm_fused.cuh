@@ -37,11 +37,12 @@ struct MarchCfg {
 };
 
 // Force, velocity and collision of one fluid node in place (fv: f on entry,
-// f* on exit; nbP: density plane at x + c_i). The FP32 compute type runs
-// the paired path of the two-pass kernel (same arithmetic, same results).
+// f* on exit; nbP: density plane at x + c_i; rho: the node's densities on
+// exit). The FP32 compute type runs the paired path of the two-pass kernel
+// (same arithmetic, same results).
 template <typename C>
 __device__ __forceinline__ void march_update(C fv[2][9], const C nbP[2][9], uint16_t fl, bool general,
-                                             const PhysK<C>& ph) {
+                                             const PhysK<C>& ph, C rho_out[2]) {
   if constexpr (sizeof(C) == 4) {
     float2 fp[9], q[9];
 #pragma unroll
@@ -49,10 +50,9 @@ __device__ __forceinline__ void march_update(C fv[2][9], const C nbP[2][9], uint
       fp[i] = f2(fv[0][i], fv[1][i]);
       q[i] = f2(nbP[0][i], nbP[1][i]);
     }
-    if (general)
-      update_pair<true>(fp, q, fl, ph);
-    else
-      update_pair<false>(fp, q, fl, ph);
+    const float2 r = general ? update_pair<true>(fp, q, fl, ph) : update_pair<false>(fp, q, fl, ph);
+    rho_out[0] = r.x;
+    rho_out[1] = r.y;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       fv[0][i] = fp[i].x;
@@ -60,6 +60,8 @@ __device__ __forceinline__ void march_update(C fv[2][9], const C nbP[2][9], uint
     }
   } else {
     const C rho[2] = {density(fv[0]), density(fv[1])};
+    rho_out[0] = rho[0];
+    rho_out[1] = rho[1];
     C F[2][2];
     interaction_force<C, true>(ph, fl, rho, nbP, F);
     C jxA, jyA, jxB, jyB;
@@ -173,7 +175,8 @@ __global__ void __launch_bounds__(MARCH_WARPS * 32, 4)
     }
     T* rrow = ring + (size_t)((y + MARCH_RING) % MARCH_RING) * 18 * 32 + lane;
     if (fluid) {
-      march_update<C>(fv, nbP, fl, general, ph);
+      C rho_unused[2];
+      march_update<C>(fv, nbP, fl, general, ph, rho_unused);
 #pragma unroll
       for (int s = 0; s < 2; ++s)
 #pragma unroll
@@ -216,9 +219,10 @@ __global__ void __launch_bounds__(MARCH_WARPS * 32, 4)
   }
 }
 
-// The single-pass kernel keeps 4- and 8-byte populations only (16-bit
-// storage needs the encoding references of the step before, which the
-// double-buffered density plane no longer holds).
+// The marching kernel keeps 4- and 8-byte populations only (16-bit storage
+// needs the encoding references of the step before, which its
+// double-buffered density plane no longer holds; the tiled schedule keeps a
+// third plane for them).
 template <typename T>
 inline bool fused_supported(const Geo&, const Phys&) {
   return sizeof(T) >= 4;

@@ -22,7 +22,9 @@ struct lbm_ctx {
   char* ws;
   size_t ws_bytes;
   void* f[2];          // population buffers (storage type)
-  void* Pbuf[2];       // two density plane pairs (compute type)
+  void* Pbuf[3];       // density plane pairs (compute type); the third only for
+                       // the tiled schedule with 16-bit storage (null otherwise)
+  char* Pbase;         // start of the density planes in the workspace
   void* P;             // Pbuf[pcur]: the densities the current populations were
                        // written with (16-bit encoding references); after a
                        // single-pass step, the densities of the current state

@@ -25,6 +25,7 @@
 #include "lbm_common.cuh"
 #include "lbm_fused.cuh"
 #include "lbm_geometry.cuh"
+#include "lbm_kernels.cuh"
 
 namespace lbm {
 
@@ -98,11 +99,17 @@ static __global__ void __launch_bounds__(TILE_LIST_THREADS) k_tile_lists(const u
 }
 
 // One CTA per tile; dynamic shared memory holds f*(t+1) of the region as
-// nine planes of component pairs, [9][TILE_RS].
+// nine planes of component pairs, [9][TILE_RS]. 16-bit storage: Pref holds
+// the densities the pulled populations were encoded with (their writers'
+// rho(t - 1)), the node encodes what it stores with its own rho(t), and
+// shared memory keeps each value as the next step will decode it (encoded
+// and decoded again), so that phase 2 sums exactly what the next step
+// pulls, like the density pass. Pref is not read for 4- and 8-byte storage.
 template <typename T>
 __global__ void __launch_bounds__(TILE_THREADS, 4)
     k_tile(const T* __restrict__ f, T* __restrict__ fo, const typename Pop<T>::C* __restrict__ P,
-           typename Pop<T>::C* __restrict__ Po, const uint16_t* __restrict__ flags,
+           const typename Pop<T>::C* __restrict__ Pref, typename Pop<T>::C* __restrict__ Po,
+           const uint16_t* __restrict__ flags,
            const uint16_t* __restrict__ entries, const int* __restrict__ offsets, const int* __restrict__ nown,
            Geo g, int ntx, PhysK<typename Pop<T>::C> ph) {
   using C = typename Pop<T>::C;
@@ -124,12 +131,6 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
   }
   const int x0 = (tile % ntx) * TILE_W, y0 = (tile / ntx) * TILE_H;
   const int korg = g.idx(x0 - 1, y0 - 1);  // padded index of slot 0
-  C ref[2][9];  // storage references: unused for 4- and 8-byte populations
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-#pragma unroll
-    for (int i = 0; i < 9; ++i) ref[q][i] = C(0);
-
   for (int b = 0; b < n_all; b += TILE_THREADS) {
     const int t = b + threadIdx.x;
     const bool valid = t < n_all;
@@ -144,6 +145,8 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
     const int row = slot / TILE_RW, col = slot - row * TILE_RW;
     const int k = korg + row * g.px + col;
     const uint16_t fl = warp_edge ? __ldg(flags + k) : uint16_t(0);
+    C ref[2][9];  // storage references (zero for 4- and 8-byte populations)
+    pull_refs<T>(Pref, g, k, fl, warp_edge, ref);
     C fv[2][9];
 #pragma unroll
     for (int i = 0; i < 9; ++i)
@@ -157,7 +160,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
       for (int i = 0; i < 9; ++i)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(f + pslot(g, i, k2 - cx_of(i) - cy_of(i) * g.px)));
     }
-    march_update<C>(fv, nbP, fl, warp_edge, ph);
+    C rho[2];
+    march_update<C>(fv, nbP, fl, warp_edge, ph, rho);
+    write_refs<T>(rho, ref);
     if (t < n_own) {
       if (!warp_border) {
 #pragma unroll
@@ -172,8 +177,8 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       V v;
-      v.x = fv[0][i];
-      v.y = fv[1][i];
+      v.x = Pop<T>::dec(Pop<T>::enc(fv[0][i], ref[0][i]), ref[0][i]);
+      v.y = Pop<T>::dec(Pop<T>::enc(fv[1][i], ref[1][i]), ref[1][i]);
       s[i * TILE_RS + slot] = v;
     }
   }
@@ -208,7 +213,8 @@ constexpr size_t tile_smem() {
 
 template <typename T>
 inline lbm_status launch_tiled(const Geo& g, const Phys& ph, const T* fin, T* fout, const typename Pop<T>::C* P,
-                               typename Pop<T>::C* Po, const uint16_t* flags, const uint16_t* entries,
+                               const typename Pop<T>::C* Pref, typename Pop<T>::C* Po, const uint16_t* flags,
+                               const uint16_t* entries,
                                const int* offsets, const int* nown, cudaStream_t stream) {
   constexpr size_t SMEM = tile_smem<T>();
   auto kern = k_tile<T>;
@@ -224,7 +230,7 @@ inline lbm_status launch_tiled(const Geo& g, const Phys& ph, const T* fin, T* fo
   }
   const int ntx = (g.nx + TILE_W - 1) / TILE_W;
   const int64_t nt = tile_count(g);
-  kern<<<(unsigned)nt, TILE_THREADS, SMEM, stream>>>(fin, fout, P, Po, flags, entries, offsets, nown, g, ntx,
+  kern<<<(unsigned)nt, TILE_THREADS, SMEM, stream>>>(fin, fout, P, Pref, Po, flags, entries, offsets, nown, g, ntx,
                                                      kphys<typename Pop<T>::C>(ph));
   return LBM_OK;
 }

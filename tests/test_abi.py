@@ -110,8 +110,8 @@ def test_argument_checks_before_any_cuda_call(lib):
 def test_tiled_schedule_workspace_without_gpu():
     """The tiled schedule adds its per-tile lists (2 bytes per region slot of
     each 32 x 14 tile plus per-tile offsets and counts, each array 256-byte
-    aligned) for 4- and 8-byte
-    storage only; an unknown schedule is rejected."""
+    aligned), and for 16-bit storage a third density plane pair; AUTO keeps
+    them for 4- and 8-byte storage only; an unknown schedule is rejected."""
     lbm.load()
     align = lambda n: (n + 255) // 256 * 256
     for nx, ny in ((8192, 8192), (100, 70), (4, 4)):
@@ -123,9 +123,14 @@ def test_tiled_schedule_workspace_without_gpu():
             assert tiled - base == extra, (nx, ny, st)
             # AUTO runs the tiled schedule for 4- and 8-byte storage
             assert lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="auto")) == tiled
-        for st in ("fp16", "bf16"):  # 16-bit storage runs the two-pass schedule
-            for k in ("tiled", "auto"):
-                assert (lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel=k))
-                        == lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="two_pass")))
+        px = -(-(32 + nx + 4) // 32) * 32  # padded pitch and rows
+        plane = px * (ny + 8)
+        for st in ("fp16", "bf16"):
+            base = lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="two_pass"))
+            # AUTO runs the two-pass schedule for 16-bit storage
+            assert lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="auto")) == base
+            # TILED adds the tile lists and a third density plane pair (FP32)
+            tiled = lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="tiled"))
+            assert tiled - base == extra + 2 * plane * 4, (nx, ny, st)
     with pytest.raises(lbm.LbmError):
         lbm.workspace_bytes(lbm.make_params(8, 8, kernel=4))

@@ -7,10 +7,11 @@ import bench
 
 
 def test_effective_schedule():
-    # 16-bit storage always runs the two-pass schedule; AUTO is tiled otherwise
+    # 16-bit storage runs the two-pass schedule unless tiled is asked for;
+    # AUTO is tiled for 4- and 8-byte storage
     for k in ("auto", "two_pass", "fused", "tiled"):
         for st in ("fp16", "bf16"):
-            assert bench.effective_schedule(k, st) == "two_pass"
+            assert bench.effective_schedule(k, st) == ("tiled" if k == "tiled" else "two_pass")
     for st in ("fp32", "fp64"):
         assert bench.effective_schedule("auto", st) == "tiled"
         for k in ("two_pass", "fused", "tiled"):
@@ -22,6 +23,7 @@ def test_l2_fetch_per_schedule():
     assert bench.l2_fetch_for("tiled", "fp64", -1) == 128
     assert bench.l2_fetch_for("two_pass", "fp32", -1) == 32
     assert bench.l2_fetch_for("auto", "fp16", -1) == 32
+    assert bench.l2_fetch_for("tiled", "fp16", -1) == 128
     assert bench.l2_fetch_for("fused", "fp32", -1) == 32
     for req in (0, 32, 64, 128):  # an explicit request wins
         assert bench.l2_fetch_for("auto", "fp32", req) == req
