@@ -157,8 +157,9 @@ def set_l2_fetch_granularity(nbytes: int) -> int:
     """Set the L2 fetch granularity hint of the current CUDA device's context
     (32, 64 or 128 bytes; lbm_set_l2_fetch_granularity) and return the
     previous value. It applies to every kernel of this process on that
-    device; the library never sets it by itself. 32 bytes is fastest for the
-    step on porous geometries."""
+    device; the library never sets it by itself. On porous geometries 128
+    bytes is fastest for the tiled schedule (the default for FP32/FP64) and
+    the batched one, 32 bytes for the two-pass schedule."""
     lib = load()
     prev = ctypes.c_int32()
     st = lib.lbm_set_l2_fetch_granularity(int(nbytes), ctypes.byref(prev))
@@ -169,6 +170,9 @@ def set_l2_fetch_granularity(nbytes: int) -> int:
 
 def make_params(nx, ny, *, tau=(1.0, 1.0), G_AB=3.0, periodic_x=False, periodic_y=False,
                 storage="fp32", kernel="auto", rho_ref=(1.0, 1.0), max_interface=0) -> LbmParams:
+    """lbm_params of the C ABI. kernel: "auto" (tiled for fp32/fp64, two-pass
+    for fp16/bf16), "two_pass", "fused" (marching single pass, fp32/fp64) or
+    "tiled"; every schedule gives the same results bit for bit."""
     p = LbmParams()
     p.nx, p.ny = int(nx), int(ny)
     p.periodic_x, p.periodic_y = int(bool(periodic_x)), int(bool(periodic_y))
