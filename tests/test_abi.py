@@ -134,3 +134,19 @@ def test_tiled_schedule_workspace_without_gpu():
             assert tiled - base == extra + 2 * plane * 4, (nx, ny, st)
     with pytest.raises(lbm.LbmError):
         lbm.workspace_bytes(lbm.make_params(8, 8, kernel=4))
+
+
+def test_binding_enums_match_header():
+    """The binding's names for status codes, storage types, schedules,
+    wetting schemes and pairings carry the values include/lbm.h declares."""
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "lbm.h")).read()
+    decl = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(LBM_[A-Z0-9_]+)\s*=\s*(\d+)", hdr)}
+    assert [decl[f"LBM_{n}"] for n in ("OK", "ERR_ARG", "ERR_STATE", "ERR_CUDA", "ERR_SPACE", "ERR_TIMEOUT")] == \
+        [lbm.OK, lbm.ERR_ARG, lbm.ERR_STATE, lbm.ERR_CUDA, lbm.ERR_SPACE, lbm.ERR_TIMEOUT]
+    assert {k: decl[f"LBM_STORE_{k.upper()}"] for k in lbm.STORAGE} == lbm.STORAGE
+    assert {k: decl[f"LBM_KERNEL_{k.upper()}"] for k in lbm.KERNEL} == lbm.KERNEL
+    assert len(lbm.KERNEL) == len([n for n in decl if n.startswith("LBM_KERNEL_")])
+    for name, hname in (("martys_chen", "MARTYS_CHEN"), ("llkc", "LLKC"), ("virtual_avg", "VIRTUAL_AVG"),
+                        ("constant", "CONSTANT")):
+        assert lbm.WETTING[name] == decl[f"LBM_WET_{hname}"]
+    assert (lbm.PAIR_CROSS, lbm.PAIR_SELF) == (decl["LBM_PAIR_CROSS"], decl["LBM_PAIR_SELF"])
