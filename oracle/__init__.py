@@ -57,8 +57,12 @@ def build(force: bool = False) -> str:
                                                   os.path.getmtime(_HDR)))
     if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math"]
+        # OpenMP over nodes (bit-identical to a serial build); a compiler
+        # without it gets the serial build
+        r = subprocess.run(base + ["-fopenmp", "-o", tmp, _SRC, "-lm"], capture_output=True)
+        if r.returncode != 0:
+            subprocess.check_call(base + ["-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -68,6 +72,10 @@ def _load():
     with _lock:
         if _lib is None:
             build()
+            # idle OpenMP threads sleep instead of spinning, so that several
+            # processes sharing the cores (parallel test ranks) do not starve
+            # one another; read once, when the OpenMP runtime starts
+            os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
             _lib = load_library(_LIB_PATH)
     return _lib
 
@@ -80,6 +88,10 @@ def load_library(path):
     d = ctypes.POINTER(ctypes.c_double)
     u8 = ctypes.POINTER(ctypes.c_ubyte)
     i32 = ctypes.POINTER(ctypes.c_int)
+    lib.oracle_set_threads.argtypes = [ctypes.c_int]
+    lib.oracle_set_threads.restype = ctypes.c_int
+    lib.oracle_max_threads.argtypes = []
+    lib.oracle_max_threads.restype = ctypes.c_int
     lib.oracle_lattice.argtypes = [i32, i32, d, i32]
     lib.oracle_d2q25.argtypes = [i32, i32, d]
     lib.oracle_d2q25.restype = ctypes.c_int
@@ -111,6 +123,16 @@ def _dp(a: np.ndarray):
 def _mp(m: np.ndarray):
     assert m.dtype == np.uint8 and m.flags.c_contiguous
     return m.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+
+
+def set_threads(n: int = 0, lib=None) -> int:
+    """Threads of the oracle's parallel node loops (0: one per core); the
+    results do not depend on it. Returns the count in effect."""
+    return (lib or _load()).oracle_set_threads(int(n))
+
+
+def max_threads(lib=None) -> int:
+    return (lib or _load()).oracle_max_threads()
 
 
 def lattice(lib=None):

@@ -11,6 +11,10 @@
  *
  * Everything is double precision, plain loops, one pass per equation, in the
  * order the paper states the method. No blocking, fusion or reordering.
+ * When built with OpenMP, the loops over nodes (or rows of nodes) run in
+ * parallel: every node's value is computed by one thread with the same
+ * arithmetic in the same order, so the results are bit for bit those of a
+ * serial build. The mass sum stays serial (its order fixes its rounding).
  *
  * Storage: f[(s*9 + i)*N + n], s = component (0 = A, 1 = B), i = D2Q9
  * direction, n = y*nx + x. The stored state is the post-streaming
@@ -31,6 +35,9 @@
  */
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #include "lbm_oracle.h"
 
@@ -85,6 +92,25 @@ static long neighbour(const oracle_params *p, int x, int y, int dx, int dy) {
 /* phi of Sec. 2: 1 for solid (or outside a non-periodic box), 0 for fluid. */
 static int phi(const unsigned char *mask, long n) {
   return (n < 0 || mask[n] != 0) ? 1 : 0;
+}
+
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n < 1) n = omp_get_num_procs();
+  omp_set_num_threads(n);
+  return n;
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 void oracle_lattice(int *cx, int *cy, double *w, int *opp) {
@@ -150,6 +176,7 @@ void oracle_densities(const oracle_params *p, const unsigned char *mask,
                       const double *f, double *rho) {
   long N = (long)p->nx * p->ny;
   for (int s = 0; s < 2; ++s)
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
       double r = 0.0;
       if (!mask[n])
@@ -162,6 +189,7 @@ void oracle_densities(const oracle_params *p, const unsigned char *mask,
  * the D2Q9 first belt (Sec. 2, last paragraph; Sec. 3.2). */
 void oracle_interface_solid(const oracle_params *p, const unsigned char *mask,
                             unsigned char *flag) {
+#pragma omp parallel for schedule(static)
   for (int y = 0; y < p->ny; ++y)
     for (int x = 0; x < p->nx; ++x) {
       long n = (long)y * p->nx + x;
@@ -184,6 +212,7 @@ void oracle_virtual_density(const oracle_params *p, const unsigned char *mask,
   oracle_interface_solid(p, mask, iface);
   int reach = (p->avg_stencil == 9) ? 1 : 2;
   for (int s = 0; s < 2; ++s)
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < p->ny; ++y)
       for (int x = 0; x < p->nx; ++x) {
         long n = (long)y * p->nx + x;
@@ -235,6 +264,7 @@ void oracle_forces(const oracle_params *p, const unsigned char *mask,
   for (int s = 0; s < 2; ++s) {
     int sb = 1 - s;                       /* sigma bar */
     int cs = (p->pairing == ORACLE_PAIR_SELF) ? s : sb;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < p->ny; ++y)
       for (int x = 0; x < p->nx; ++x) {
         long n = (long)y * p->nx + x;
@@ -270,6 +300,7 @@ void oracle_velocity(const oracle_params *p, const unsigned char *mask,
                      const double *f, const double *rho, const double *F,
                      double *u) {
   long N = (long)p->nx * p->ny;
+#pragma omp parallel for schedule(static)
   for (long n = 0; n < N; ++n) {
     double jx = 0.0, jy = 0.0;
     if (!mask[n]) {
@@ -309,9 +340,10 @@ void oracle_collide(const oracle_params *p, const unsigned char *mask,
                     const double *f, const double *rho, const double *u,
                     const double *F, double *fpost) {
   long N = (long)p->nx * p->ny;
-  double feq[9], S[9];
   for (int s = 0; s < 2; ++s)
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
+      double feq[9], S[9];
       if (mask[n]) {
         for (int i = 0; i < 9; ++i) fpost[(s * 9 + i) * N + n] = 0.0;
         continue;
@@ -335,6 +367,7 @@ void oracle_stream(const oracle_params *p, const unsigned char *mask,
   for (int s = 0; s < 2; ++s)
     for (int i = 0; i < 9; ++i) {
       int oi = opposite(i);
+#pragma omp parallel for schedule(static)
       for (int y = 0; y < p->ny; ++y)
         for (int x = 0; x < p->nx; ++x) {
           long n = (long)y * p->nx + x;
@@ -357,9 +390,10 @@ int oracle_init(const oracle_params *p, const unsigned char *mask,
                 const double *uy, double *f) {
   if (oracle_check(p, mask)) return 1;
   long N = (long)p->nx * p->ny;
-  double feq[9];
   for (int s = 0; s < 2; ++s)
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
+      double feq[9];
       const double *r = s ? rhoB : rhoA;
       double vx = ux ? ux[n] : 0.0, vy = uy ? uy[n] : 0.0;
       oracle_equilibrium(mask[n] ? 0.0 : r[n], vx, vy, feq);

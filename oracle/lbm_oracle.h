@@ -41,6 +41,10 @@ typedef struct {
   int avg_stencil;   /* 25 (D2Q25, the paper's choice) or 9 */
 } oracle_params;
 
+/* Threads of the parallel loops (OpenMP builds; n < 1: one per core).
+ * Returns the number set (1 in a serial build). Results do not depend on it. */
+int oracle_set_threads(int n);
+int oracle_max_threads(void);
 void oracle_lattice(int *cx, int *cy, double *w, int *opp);
 int oracle_d2q25(int *ex, int *ey, double *wt);
 int oracle_check(const oracle_params *p, const unsigned char *mask);

@@ -211,7 +211,7 @@ lbm_status step_fused(lbm_ctx* c, int nsteps) {
     if (c->n_tiles > 0) {
       s = launch(c, LBM_KC_FUSED, "k_tile", [&] {
         ls = launch_tiled<T>(c->g, c->ph, fin, fout, Pin, Pin, Pout, c->flags, c->tile_entries, c->tile_off,
-                             c->tile_nown, c->stream);
+                             c->tile_nown, &c->tile_smem_set, c->stream);
       });
     } else {
       s = launch(c, LBM_KC_FUSED, "k_march", [&] {
@@ -261,7 +261,7 @@ lbm_status step_tiled16(lbm_ctx* c, int nsteps) {
     lbm_status ls = LBM_OK;
     s = launch(c, LBM_KC_FUSED, "k_tile", [&] {
       ls = launch_tiled<T>(c->g, c->ph, fin, fout, P, Pref, Po, c->flags, c->tile_entries, c->tile_off,
-                           c->tile_nown, c->stream);
+                           c->tile_nown, &c->tile_smem_set, c->stream);
     });
     if (ls) return fail(c, ls, "tiled kernel launch rejected");
     if (s) return s;

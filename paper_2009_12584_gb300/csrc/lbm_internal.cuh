@@ -38,6 +38,7 @@ struct lbm_ctx {
   int* tile_off;       // tiled schedule: first entry of each tile, total at [ntiles]
   int* tile_nown;      // tiled schedule: owned fluid nodes of each tile
   int64_t n_tiles;
+  bool tile_smem_set;  // k_tile's dynamic shared memory limit raised on this context's device
   int* scan_counts;    // per-block interface counts / offsets
   int* small;          // [0] error count, [1] interface total, [2] fluid total
   double* partial;     // mass partial sums

@@ -292,9 +292,13 @@ __device__ __forceinline__ void ldP_line(const C* __restrict__ P, int64_t k, C& 
     asm("ld.global.nc.L2::128B.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(P + 2 * k));
 }
 
-template <typename C, bool AVG9>
-__device__ __forceinline__ void virtual_density(const C* __restrict__ P, uint32_t msk, const Geo& g, int k,
-                                                const PhysK<C>& ph, C& v0, C& v1) {
+// Eq. 8 at one interface-solid cell: msk holds its fluid neighbours (bit
+// (dy + 2) * 5 + (dx + 2)), load(dx, dy, a, b) fetches the densities of
+// neighbour (dx, dy); the sums run in a fixed order, so every caller (the
+// plane-based pass and the shared-memory pass of the halo schedule) gets
+// the same bits.
+template <typename C, bool AVG9, typename Load>
+__device__ __forceinline__ void virtual_density_at(uint32_t msk, const PhysK<C>& ph, Load&& load, C& v0, C& v1) {
   constexpr int REACH = AVG9 ? 1 : 2;
   constexpr int NB = (2 * REACH + 1) * (2 * REACH + 1);
   C p0[NB], p1[NB];
@@ -304,7 +308,7 @@ __device__ __forceinline__ void virtual_density(const C* __restrict__ P, uint32_
     for (int dx = -REACH; dx <= REACH; ++dx) {
       const int j = (dy + REACH) * (2 * REACH + 1) + (dx + REACH);
       p0[j] = p1[j] = C(0);
-      if ((msk >> ((dy + 2) * 5 + (dx + 2))) & 1u) ldP_line(P, k + dx + dy * g.px, p0[j], p1[j]);
+      if ((msk >> ((dy + 2) * 5 + (dx + 2))) & 1u) load(dx, dy, p0[j], p1[j]);
     }
   C num0 = 0, num1 = 0, den = 0;
 #pragma unroll
@@ -327,6 +331,13 @@ __device__ __forceinline__ void virtual_density(const C* __restrict__ P, uint32_
     }
   v0 = ph.chi[0] * num0 / den;
   v1 = ph.chi[1] * num1 / den;
+}
+
+template <typename C, bool AVG9>
+__device__ __forceinline__ void virtual_density(const C* __restrict__ P, uint32_t msk, const Geo& g, int k,
+                                                const PhysK<C>& ph, C& v0, C& v1) {
+  virtual_density_at<C, AVG9>(msk, ph, [&](int dx, int dy, C& a, C& b) { ldP_line(P, k + dx + dy * g.px, a, b); },
+                              v0, v1);
 }
 
 template <typename C>

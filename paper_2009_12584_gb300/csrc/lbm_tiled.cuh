@@ -29,12 +29,28 @@
 
 namespace lbm {
 
-constexpr int TILE_W = 32, TILE_H = 14;     // owned nodes per tile
+#ifndef LBM_TILE_W
+#define LBM_TILE_W 32
+#endif
+#ifndef LBM_TILE_H
+#define LBM_TILE_H 14
+#endif
+#ifndef LBM_TILE_THREADS
+#define LBM_TILE_THREADS 256
+#endif
+#ifndef LBM_TILE_MINB
+#define LBM_TILE_MINB 4
+#endif
+#ifndef LBM_TILE_AHEAD
+#define LBM_TILE_AHEAD 512
+#endif
+constexpr int TILE_W = LBM_TILE_W, TILE_H = LBM_TILE_H;  // owned nodes per tile
 constexpr int TILE_RW = TILE_W + 2;         // region pitch (one ring node each side)
 constexpr int TILE_RH = TILE_H + 2;
 constexpr int TILE_RS = TILE_RW * TILE_RH;  // region slots
-constexpr int TILE_THREADS = 256;           // k_tile
-constexpr int TILE_AHEAD = 512;             // tiles between a CTA and the one whose entries it prefetches
+constexpr int TILE_THREADS = LBM_TILE_THREADS;  // k_tile
+constexpr int TILE_MINB = LBM_TILE_MINB;    // k_tile CTAs per SM the registers must allow
+constexpr int TILE_AHEAD = LBM_TILE_AHEAD;  // tiles between a CTA and the one whose entries it prefetches
 constexpr int TILE_LIST_THREADS = 256;      // k_tile_lists
 static_assert(TILE_RS <= 2048, "slots must fit the 11 slot bits of an entry");
 
@@ -106,7 +122,7 @@ static __global__ void __launch_bounds__(TILE_LIST_THREADS) k_tile_lists(const u
 // and decoded again), so that phase 2 sums exactly what the next step
 // pulls, like the density pass. Pref is not read for 4- and 8-byte storage.
 template <typename T>
-__global__ void __launch_bounds__(TILE_THREADS, 4)
+__global__ void __launch_bounds__(TILE_THREADS, TILE_MINB)
     k_tile(const T* __restrict__ f, T* __restrict__ fo, const typename Pop<T>::C* __restrict__ P,
            const typename Pop<T>::C* __restrict__ Pref, typename Pop<T>::C* __restrict__ Po,
            const uint16_t* __restrict__ flags,
@@ -211,22 +227,19 @@ constexpr size_t tile_smem() {
   return (size_t)9 * TILE_RS * sizeof(typename CPair<typename Pop<T>::C>::V);
 }
 
+// Launch one tiled step. *smem_set records, per context (one device), that
+// the kernel's dynamic shared memory limit has been raised.
 template <typename T>
 inline lbm_status launch_tiled(const Geo& g, const Phys& ph, const T* fin, T* fout, const typename Pop<T>::C* P,
                                const typename Pop<T>::C* Pref, typename Pop<T>::C* Po, const uint16_t* flags,
-                               const uint16_t* entries,
-                               const int* offsets, const int* nown, cudaStream_t stream) {
+                               const uint16_t* entries, const int* offsets, const int* nown, bool* smem_set,
+                               cudaStream_t stream) {
   constexpr size_t SMEM = tile_smem<T>();
   auto kern = k_tile<T>;
-  if (SMEM > 48 * 1024) {
-    static bool configured[64] = {};  // the attribute is set per function and device
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LBM_ERR_CUDA;
-    if (!configured[dev]) {
-      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM) != cudaSuccess)
-        return LBM_ERR_CUDA;
-      configured[dev] = true;
-    }
+  if (SMEM > 48 * 1024 && !*smem_set) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM) != cudaSuccess)
+      return LBM_ERR_CUDA;
+    *smem_set = true;
   }
   const int ntx = (g.nx + TILE_W - 1) / TILE_W;
   const int64_t nt = tile_count(g);
