@@ -94,6 +94,12 @@ typedef enum {
  *   bytes per ring-extended region slot (about 2.4 bytes per node), and for
  *   16-bit storage by a third density plane (8 bytes per padded node), since
  *   a 16-bit step decodes with the densities of the step before.
+ * HALO: one kernel per step and no density plane: each CTA takes a 32 x 14
+ *   tile, recomputes rho(t) from the pulled populations for the tile and the
+ *   1 to 3 node rings its force and Eq. 8 reach (3 for the D2Q25 average, 2
+ *   for the D2Q9 average, 1 for the other schemes), evaluates Eq. 8 in
+ *   shared memory and updates its own nodes. 4- and 8-byte storage (16-bit
+ *   storage runs TWO_PASS); the workspace grows by about 4 bytes per node.
  * AUTO picks the schedule measured fastest on GB300: TILED for 4- and 8-byte
  * storage (a quarter fewer bytes than TWO_PASS and 8% faster on the 8192^2
  * porous medium; its lists are then built as for TILED), TWO_PASS for 16-bit
@@ -102,7 +108,8 @@ typedef enum {
   LBM_KERNEL_AUTO = 0,
   LBM_KERNEL_TWO_PASS = 1,
   LBM_KERNEL_FUSED = 2,
-  LBM_KERNEL_TILED = 3
+  LBM_KERNEL_TILED = 3,
+  LBM_KERNEL_HALO = 4
 } lbm_kernel;
 
 typedef struct {

@@ -39,8 +39,8 @@ bool make_geo(const lbm_params* p, Geo* g) {
 }
 
 struct Layout {
-  size_t f, P, flags, list, imask, flist, tent, toff, tnown, counts, small, partial, mass, smask, stage, dpart,
-      total;
+  size_t f, P, flags, list, imask, flist, tent, toff, tnown, hent, hoff, hcnt, hmask, counts, small, partial, mass,
+      smask, stage, dpart, total;
 };
 
 // Whether a context keeps the per-tile lists of the tiled schedule (the
@@ -49,6 +49,13 @@ struct Layout {
 bool uses_tiles(const lbm_params* p) {
   const bool wide = p->storage == LBM_STORE_FP32 || p->storage == LBM_STORE_FP64;
   return p->kernel == LBM_KERNEL_TILED || (p->kernel == LBM_KERNEL_AUTO && wide);
+}
+
+// Whether a context keeps the per-tile lists of the halo schedule (4- and
+// 8-byte storage; 16-bit storage runs the two-pass schedule instead).
+bool uses_halo(const lbm_params* p) {
+  const bool wide = p->storage == LBM_STORE_FP32 || p->storage == LBM_STORE_FP64;
+  return p->kernel == LBM_KERNEL_HALO && wide;
 }
 
 // The tiled schedule with 16-bit storage keeps a third density plane: a step
@@ -77,6 +84,11 @@ bool layout(const lbm_params* p, const Geo& g, Layout* L) {
   L->tent = off;     off = align_up(off + (size_t)nt * TILE_RS * 2, A);
   L->toff = off;     off = align_up(off + (size_t)(nt ? nt + 1 : 0) * 4, A);
   L->tnown = off;    off = align_up(off + (size_t)nt * 4, A);
+  const int64_t nh = uses_halo(p) ? halo_tile_count(g) : 0;
+  L->hent = off;     off = align_up(off + (size_t)nh * HALO_RS * 2, A);
+  L->hoff = off;     off = align_up(off + (size_t)(nh ? nh + 1 : 0) * 4, A);
+  L->hcnt = off;     off = align_up(off + (size_t)nh * 16, A);
+  L->hmask = off;    off = align_up(off + (size_t)nh * HALO_MW * 4, A);
   L->counts = off;   off = align_up(off + (size_t)scan_blocks * 4, A);
   L->small = off;    off = align_up(off + 64, A);
   L->partial = off;  off = align_up(off + 2 * MASS_BLOCKS * 8, A);
@@ -277,9 +289,30 @@ lbm_status step_tiled16(lbm_ctx* c, int nsteps) {
   return LBM_OK;
 }
 
+// Halo schedule: one kernel per step, densities recomputed per tile from the
+// populations (no density plane).
+template <typename T>
+lbm_status step_halo(lbm_ctx* c, int nsteps) {
+  for (int t = 0; t < nsteps; ++t) {
+    const T* fin = (const T*)c->f[c->cur];
+    T* fout = (T*)c->f[c->cur ^ 1];
+    lbm_status ls = LBM_OK;
+    lbm_status s = launch(c, LBM_KC_FUSED, "k_halo", [&] {
+      ls = launch_halo<T>(c->g, c->ph, fin, fout, c->flags, c->halo_entries, c->halo_off, c->halo_cnt,
+                          c->halo_fmask, c->stream);
+    });
+    if (ls) return fail(c, ls, "halo kernel launch rejected");
+    if (s) return s;
+    c->cur ^= 1;
+    c->p_valid = false;
+  }
+  return LBM_OK;
+}
+
 template <typename T>
 lbm_status do_step(lbm_ctx* c, int nsteps) {
   if constexpr (sizeof(T) >= 4) {  // the marching kernel stores 4- and 8-byte populations only
+    if (c->n_halo_tiles > 0) return step_halo<T>(c, nsteps);
     if (c->prm.kernel == LBM_KERNEL_FUSED && fused_supported<T>(c->g, c->ph)) return step_fused<T>(c, nsteps);
     const bool tiled = c->prm.kernel == LBM_KERNEL_TILED || c->prm.kernel == LBM_KERNEL_AUTO;
     if (tiled && c->n_tiles > 0) return step_fused<T>(c, nsteps);
@@ -342,7 +375,7 @@ bool valid_params(const lbm_params* p) {
   if (p->nx < 4 || p->ny < 4) return false;
   if (!(p->tau[0] > 0.5) || !(p->tau[1] > 0.5)) return false;
   if (p->storage < LBM_STORE_FP32 || p->storage > LBM_STORE_BF16) return false;
-  if (p->kernel < LBM_KERNEL_AUTO || p->kernel > LBM_KERNEL_TILED) return false;
+  if (p->kernel < LBM_KERNEL_AUTO || p->kernel > LBM_KERNEL_HALO) return false;
   if (p->max_interface < 0) return false;
   return true;
 }
@@ -414,6 +447,11 @@ lbm_status lbm_create(const lbm_params* params, void* d_workspace, size_t bytes,
   c->tile_entries = c->n_tiles ? (uint16_t*)(c->ws + L.tent) : nullptr;
   c->tile_off = c->n_tiles ? (int*)(c->ws + L.toff) : nullptr;
   c->tile_nown = c->n_tiles ? (int*)(c->ws + L.tnown) : nullptr;
+  c->n_halo_tiles = uses_halo(params) ? halo_tile_count(g) : 0;
+  c->halo_entries = c->n_halo_tiles ? (uint16_t*)(c->ws + L.hent) : nullptr;
+  c->halo_off = c->n_halo_tiles ? (int*)(c->ws + L.hoff) : nullptr;
+  c->halo_cnt = c->n_halo_tiles ? (int4*)(c->ws + L.hcnt) : nullptr;
+  c->halo_fmask = c->n_halo_tiles ? (uint32_t*)(c->ws + L.hmask) : nullptr;
   c->scan_counts = (int*)(c->ws + L.counts);
   c->small = (int*)(c->ws + L.small);
   c->partial = (double*)(c->ws + L.partial);
@@ -508,6 +546,20 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* d_mask) {
     k_tile_lists<<<nt, TILE_LIST_THREADS, 0, c->stream>>>(c->flags, g, ntx, c->tile_off, nullptr, nullptr,
                                                      c->tile_entries);
     if ((s = after_launch(c, "k_tile_lists(write)"))) return s;
+  }
+  if (c->n_halo_tiles > 0) {
+    // per-tile lists of the halo schedule: counts and fluid bitmasks,
+    // offsets (fixed-order scan, total at halo_off[n_halo_tiles]), entries
+    const int ntx = (g.nx + HALO_W - 1) / HALO_W;
+    const int nt = (int)c->n_halo_tiles;
+    k_halo_lists<<<nt, HALO_LIST_THREADS, 0, c->stream>>>(c->flags, g, ntx, nullptr, c->halo_off, c->halo_cnt,
+                                                          c->halo_fmask, nullptr);
+    if ((s = after_launch(c, "k_halo_lists(count)"))) return s;
+    k_iface_scan<<<1, 1024, 0, c->stream>>>(c->halo_off, nt, c->halo_off + nt);
+    if ((s = after_launch(c, "k_iface_scan(halo)"))) return s;
+    k_halo_lists<<<nt, HALO_LIST_THREADS, 0, c->stream>>>(c->flags, g, ntx, c->halo_off, nullptr, nullptr, nullptr,
+                                                          c->halo_entries);
+    if ((s = after_launch(c, "k_halo_lists(write)"))) return s;
   }
   c->has_geometry = true;
   return LBM_OK;

@@ -5,6 +5,7 @@
 #include "lbm.h"
 #include "lbm_fused.cuh"
 #include "lbm_geometry.cuh"
+#include "lbm_halo.cuh"
 #include "lbm_kernels.cuh"
 #include "lbm_tiled.cuh"
 
@@ -39,6 +40,11 @@ struct lbm_ctx {
   int* tile_nown;      // tiled schedule: owned fluid nodes of each tile
   int64_t n_tiles;
   bool tile_smem_set;  // k_tile's dynamic shared memory limit raised on this context's device
+  uint16_t* halo_entries; // halo schedule: per-tile lists of region slots (null if unused)
+  int* halo_off;       // halo schedule: first entry of each tile, total at [n_halo_tiles]
+  int4* halo_cnt;      // halo schedule: cumulative counts (own, +ring 1, +ring 2, +ring 3) per tile
+  uint32_t* halo_fmask; // halo schedule: fluid bitmask of each tile's region
+  int64_t n_halo_tiles;
   int* scan_counts;    // per-block interface counts / offsets
   int* small;          // [0] error count, [1] interface total, [2] fluid total
   double* partial;     // mass partial sums

@@ -20,7 +20,7 @@ OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_SPACE, ERR_TIMEOUT = range(6)
 WET_MARTYS_CHEN, WET_LLKC, WET_VIRTUAL_AVG, WET_CONSTANT = range(4)
 PAIR_CROSS, PAIR_SELF = 0, 1
 STORAGE = {"fp32": 0, "fp64": 1, "fp16": 2, "bf16": 3}
-KERNEL = {"auto": 0, "two_pass": 1, "fused": 2, "tiled": 3}
+KERNEL = {"auto": 0, "two_pass": 1, "fused": 2, "tiled": 3, "halo": 4}
 WETTING = {"martys_chen": 0, "mc": 0, "llkc": 1, "virtual_avg": 2, "improved": 2, "constant": 3}
 
 

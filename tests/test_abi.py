@@ -133,7 +133,26 @@ def test_tiled_schedule_workspace_without_gpu():
             tiled = lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="tiled"))
             assert tiled - base == extra + 2 * plane * 4, (nx, ny, st)
     with pytest.raises(lbm.LbmError):
-        lbm.workspace_bytes(lbm.make_params(8, 8, kernel=4))
+        lbm.workspace_bytes(lbm.make_params(8, 8, kernel=5))
+
+
+def test_halo_schedule_workspace_without_gpu():
+    """The halo schedule adds its per-tile lists: 2 bytes per slot of each
+    tile's (32 + 6) x (14 + 6) region, per-tile offsets, four cumulative ring
+    counts and a fluid bitmask of the region (24 words), each array 256-byte
+    aligned; 16-bit storage runs the two-pass schedule and keeps none."""
+    lbm.load()
+    align = lambda n: (n + 255) // 256 * 256
+    for nx, ny in ((8192, 8192), (100, 70), (4, 4)):
+        nt = -(-nx // 32) * -(-ny // 14)
+        extra = align(nt * 38 * 20 * 2) + align((nt + 1) * 4) + align(nt * 16) + align(nt * 24 * 4)
+        for st in ("fp32", "fp64"):
+            base = lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="two_pass"))
+            halo = lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="halo"))
+            assert halo - base == extra, (nx, ny, st)
+        for st in ("fp16", "bf16"):
+            base = lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="two_pass"))
+            assert lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="halo")) == base
 
 
 def test_binding_enums_match_header():

@@ -22,7 +22,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 from paper_2009_12584_gb300 import lbm  # noqa: E402
 
-KERNELS = ["two_pass", "fused", "tiled"]
+KERNELS = ["two_pass", "fused", "tiled", "halo"]
 
 WETTINGS = {
     "mc": (dict(bc=oracle.BC_MARTYS_CHEN, G_s=(-0.2, 0.2)), ("martys_chen", dict(G_s=(-0.2, 0.2)))),

@@ -1,9 +1,23 @@
 """Physics pins of the oracle against what the paper prints and what the
 mean-field theory of the model fixes (approximate, stated tolerances):
 
-- flat-interface coexistence: ln(a/b) = G (a - b) for psi = rho (mean field);
-- Laplace law with the surface tension printed in Sec. 4 (sigma = 0.026 at
-  G_AB = 3, read as Delta p = 2 sigma / R, see the design notes);
+- flat-interface coexistence: ln(a/b) = G (a - b) for psi = rho (mean field),
+  the pin of the interaction force's magnitude;
+- Laplace law: Delta p linear in 1/R through the origin. The oracle's 2-D
+  slope (sigma of Delta p = sigma / R) is 0.052; the paper prints
+  sigma = 0.026 for G_AB = 3 (Sec. 4), which it matches only if the paper's
+  sigma is half the 2-D slope (Delta p = 2 sigma / R). That reading is
+  fitted to the oracle, so the test pins the law's form and the slope's
+  value against a fixed number, not an independent surface tension;
+- the contact angles the paper prints on a flat, grid-aligned wall (Sec. 3.1
+  set-up: walls on the borders, R0 droplet, 1 / 0.055): the improved
+  scheme's 71 deg at xi = -0.2 within 5 deg, and the difference between the
+  LLKC angle at G_w = -0.5 and the Martys-Chen angle at G_w = -0.2 (63 - 55 =
+  8 deg) within 5 deg. The second decides the reading of Eq. 7 for LLKC:
+  pairing the force on sigma with the other component's solid density (as
+  printed) gives +6 deg, the alternative (self) pairing -24 deg. The printed
+  absolute angles of those two schemes are not reproduced (the oracle gives
+  about 65 and 71 deg at R0 = 12 and 18);
 - the paper's central observation (Sec. 3): on a staircase wall inclined at
   20 deg a Martys-Chen or LLKC droplet slides at a speed of order 1e-2, a
   droplet under the improved virtual-density scheme stays at rest;
@@ -51,6 +65,40 @@ def test_flat_interface_coexistence():
     assert np.abs(u).max() < 1e-5
 
 
+def _paper_flat_wall_angle(kw, nx=140, ny=70, R0=12, steps=6000):
+    """Equilibrium angle on the Sec. 3.1 set-up with a grid-aligned plane
+    (beta = 0): walls on every border, the plane tangent to a sharp droplet
+    of radius R0 centred in the box. Contour points near the box's corners,
+    where fluid from the wetting layer collects (Sec. 3.1), are left out."""
+    mask = inputs.inclined_wall_mask(nx, ny, 0.0, R0)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, ny / 2, R0)
+    o = oracle.Oracle(nx, ny, mask, **kw).init(rA, rB).step(steps)
+    rho, _, _, _ = o.fields()
+    wall_y = math.ceil(ny / 2 - R0) - 0.5  # halfway between the plane's last solid and first fluid row
+    return diag.contact_angle(rho[0], mask, (0.0, wall_y), 0.0, box=(6, nx - 7, wall_y, ny - 7))[0]
+
+
+def test_improved_scheme_printed_contact_angle():
+    """xi = -0.2 gives 71 deg (Sec. 4). With Eq. 7 as printed (the force on A
+    sees the virtual density of B), the paper's hydrophilic xi < 0 maps to
+    chi^A = 1 - xi, chi^B = 1 + xi."""
+    th = _paper_flat_wall_angle(dict(bc=oracle.BC_VIRTUAL_AVG, G_s=(3.0, 3.0), chi=(1.2, 0.8)))
+    assert abs(th - paper_value("theta_improved_xi-0.2")) < 5.0, th
+
+
+def test_llkc_minus_martys_chen_angle_decides_pairing():
+    """LLKC at G_w = -0.5 wets less than Martys-Chen at G_w = -0.2 by the
+    printed 63 - 55 = 8 deg (within 5 deg) with Eq. 7's cross pairing; the
+    self pairing makes LLKC wet far more (about -24 deg), so it is not the
+    paper's scheme."""
+    mc = _paper_flat_wall_angle(dict(bc=oracle.BC_MARTYS_CHEN, G_s=(-0.2, 0.2)))
+    cross = _paper_flat_wall_angle(dict(bc=oracle.BC_LLKC, G_s=(-0.5, 0.5), pairing=oracle.PAIR_CROSS))
+    self_ = _paper_flat_wall_angle(dict(bc=oracle.BC_LLKC, G_s=(-0.5, 0.5), pairing=oracle.PAIR_SELF))
+    printed = paper_value("theta_llkc_gw-0.5") - paper_value("theta_mc_gw-0.2")
+    assert abs((cross - mc) - printed) < 5.0, (mc, cross)
+    assert abs((self_ - mc) - printed) > 15.0, (mc, self_)
+
+
 def test_laplace_law_surface_tension():
     G = paper_value("G_AB")
     sigma_paper = paper_value("sigma")
@@ -67,7 +115,8 @@ def test_laplace_law_surface_tension():
         inv_R.append(1 / R_eq)
         dp.append(p[n // 2, n // 2] - p[0, 0])
     slope, icpt = np.polyfit(inv_R, dp, 1)
-    # Delta p = 2 sigma / R with the printed sigma, within 10%
+    # the 2-D slope sigma_2D = Delta p R is 0.052 (twice the printed 0.026,
+    # see the module docstring), within 10%
     assert abs(slope / 2 - sigma_paper) / sigma_paper < 0.10, slope
     assert abs(icpt) < 0.1 * min(dp)
 
