@@ -71,9 +71,11 @@ typedef enum { LBM_PAIR_CROSS = 0, LBM_PAIR_SELF = 1 } lbm_pairing;
 
 /* Storage type of the populations. Arithmetic is FP32 for FP32/FP16/BF16
  * and FP64 for FP64. FP16/BF16 store each population as its deviation from
- * w_i times the density of the node that wrote it (kept in a density plane
- * of the workspace), so the 16 bits carry the non-equilibrium and velocity
- * part only. */
+ * a reference its writer and reader both know: w_i times the density of the
+ * node that wrote it (kept in a density plane of the workspace), or, with
+ * lbm_params.velocity_refs, w_i rho (1 + 3 c_i . u) with that node's
+ * velocity too, so the 16 bits carry the non-equilibrium (and, without
+ * velocity_refs, the velocity) part only. */
 typedef enum {
   LBM_STORE_FP32 = 0,
   LBM_STORE_FP64 = 1,
@@ -100,6 +102,14 @@ typedef enum {
  *   for the D2Q9 average, 1 for the other schemes), evaluates Eq. 8 in
  *   shared memory and updates its own nodes. 4- and 8-byte storage (16-bit
  *   storage runs TWO_PASS); the workspace grows by about 4 bytes per node.
+ * TMA: the TILED schedule (same lists, same results bit for bit) with a
+ *   persistent CTA per SM whose tiles' inputs, the nine population planes
+ *   and the density plane over each tile's (32 + 4) x (14 + 4) window, are
+ *   copied into shared memory by the Tensor Memory Accelerator, double
+ *   buffered so that the next tile's copy overlaps the current tile's
+ *   update. FP32 storage (other storage runs TILED). A copy not seen to
+ *   complete within a bounded wait stops the kernel and is reported as
+ *   LBM_ERR_TIMEOUT by the next lbm_sync, lbm_mass or lbm_step_profiled.
  * AUTO picks the schedule measured fastest on GB300: TILED for 4- and 8-byte
  * storage (a quarter fewer bytes than TWO_PASS and 8% faster on the 8192^2
  * porous medium; its lists are then built as for TILED), TWO_PASS for 16-bit
@@ -109,7 +119,8 @@ typedef enum {
   LBM_KERNEL_TWO_PASS = 1,
   LBM_KERNEL_FUSED = 2,
   LBM_KERNEL_TILED = 3,
-  LBM_KERNEL_HALO = 4
+  LBM_KERNEL_HALO = 4,
+  LBM_KERNEL_TMA = 5
 } lbm_kernel;
 
 typedef struct {
@@ -123,6 +134,12 @@ typedef struct {
   double rho_ref[2];          /* reserved, ignored (set to 0) */
   int64_t max_interface;      /* capacity of the interface-solid list;
                                  0 -> nx*ny (always enough) */
+  int32_t velocity_refs;      /* 16-bit storage only: 1 stores each population
+                                 as its deviation from w_i rho (1 + 3 c_i . u)
+                                 of its writer (rho and u kept in the
+                                 workspace, u as FP16: 8 more bytes per
+                                 padded node, slower, more accurate for moving
+                                 fluid); 0 (default) from w_i rho */
 } lbm_params;
 
 typedef struct {
@@ -298,6 +315,17 @@ lbm_status lbm_run_host(lbm_ctx* ctx, const lbm_wetting_params* w, const uint8_t
                         double* h_rhoA_out, double* h_rhoB_out, double* h_ux_out,
                         double* h_uy_out);
 
+/* lbm_run_host with FP32 host arrays: initial densities in, densities and
+ * velocity out (float [ny][nx] each; outputs may be NULL). The inputs are
+ * widened to FP64 on the device and the moments rounded to FP32 there, so
+ * the host transfers carry half the bytes (9 + 16 bytes per node against
+ * 17 + 32). Same staging, stream and synchronisation as lbm_run_host; the
+ * paper has no counterpart. */
+lbm_status lbm_run_host_f32(lbm_ctx* ctx, const lbm_wetting_params* w, const uint8_t* h_mask,
+                            const float* h_rhoA, const float* h_rhoB, int32_t nsteps,
+                            float* h_rhoA_out, float* h_rhoB_out, float* h_ux_out,
+                            float* h_uy_out);
+
 /* Per-component mass of two density fields without any device allocation
  * and without a workspace. The paper has no counterpart: this is a service
  * for callers that cannot allocate device memory at the point they need the
@@ -323,8 +351,11 @@ lbm_status lbm_run_host(lbm_ctx* ctx, const lbm_wetting_params* w, const uint8_t
  *
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture. Returns LBM_ERR_CUDA if the lookup or a launch
- * fails. */
+ * before any stream capture. The address is remembered per CUDA context
+ * (by the driver's context identifier), so a context created again after
+ * cudaDeviceReset gets a fresh lookup. Returns LBM_ERR_CUDA if the lookup or
+ * a launch fails, or if an earlier error is pending (cudaPeekAtLastError;
+ * the pending error is left for the caller). */
 lbm_status lbm_field_mass_noalloc(const double* d_rhoA, const double* d_rhoB,
                                   const uint8_t* d_mask, int32_t nx, int32_t ny,
                                   double* d_out, void* cuda_stream);
@@ -333,7 +364,12 @@ lbm_status lbm_field_mass_noalloc(const double* d_rhoA, const double* d_rhoB,
  * Many independent simulations (contexts with their own geometry, wetting
  * and size, all of the same storage type on one device) advance together:
  * each step is one launch per kernel class over all of them, and repeated
- * steps replay a CUDA graph. The batch keeps pointers to the contexts; they
+ * steps replay a CUDA graph (kernel nodes, one per launch; the batch is not
+ * one persistent kernel). Two schedules: TWO_PASS (density, Eq. 8 and
+ * collide launches over the members' fluid lists, any storage) and TILED
+ * (the Eq. 8 launch and one tiled single-pass launch over all members'
+ * 32 x 14 tiles; 4- and 8-byte storage, members created with
+ * LBM_KERNEL_AUTO or LBM_KERNEL_TILED so that they keep tile lists). The batch keeps pointers to the contexts; they
  * must outlive it, keep their geometry and wetting, and may still be
  * queried individually (lbm_moments, lbm_mass, ...) between batch steps.
  * The batch snapshots which members use the improved scheme at creation. */
@@ -357,12 +393,22 @@ lbm_status lbm_batch_set_graph_steps(lbm_batch* b, int32_t steps);
  * (synchronising on that small copy), then enqueues the work. */
 lbm_status lbm_batch_step(lbm_batch* b, int32_t nsteps);
 
-/* Time the candidate configurations (128 or 256 threads per block for the
- * density and collide kernels; 2, 8 or 32 steps per graph replay) on the
- * batch itself, keep the fastest, and write {threads, steps} to h_choice (may
- * be NULL). Advances every member by the steps it times (about 6 x
- * trial_steps plus warm-up). */
+/* Time the candidate configurations (the two-pass schedule at 128 or 256
+ * threads per block, and the tiled schedule when available; 2, 8 or 32
+ * steps per graph replay) on the batch itself, keep the fastest, and write
+ * {threads per block, steps} to h_choice (may be NULL; lbm_batch_config
+ * tells the schedule). Advances every member by the steps it times (about
+ * 9 x trial_steps plus warm-up). */
 lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, int32_t* h_choice);
+
+/* Select the schedule (LBM_KERNEL_TWO_PASS, the default, or
+ * LBM_KERNEL_TILED); rebuilds the replay graph. LBM_ERR_ARG for another
+ * value or TILED without 4-/8-byte storage and member tile lists. */
+lbm_status lbm_batch_set_schedule(lbm_batch* b, int32_t kernel);
+
+/* Current configuration: h_cfg[3] = {schedule (lbm_kernel), threads per
+ * block, steps per graph replay (0: no graph)}. */
+lbm_status lbm_batch_config(const lbm_batch* b, int32_t* h_cfg);
 
 /* Kernels launched by the batch so far (graph replays count their nodes). */
 int64_t lbm_batch_launch_count(const lbm_batch* b);

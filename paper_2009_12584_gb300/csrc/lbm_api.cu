@@ -39,7 +39,7 @@ bool make_geo(const lbm_params* p, Geo* g) {
 }
 
 struct Layout {
-  size_t f, P, flags, list, imask, flist, tent, toff, tnown, hent, hoff, hcnt, hmask, counts, small, partial, mass,
+  size_t f, P, U, flags, list, imask, flist, tent, toff, tnown, hent, hoff, hcnt, hmask, counts, small, partial, mass,
       smask, stage, dpart, total;
 };
 
@@ -48,8 +48,11 @@ struct Layout {
 // only when asked for).
 bool uses_tiles(const lbm_params* p) {
   const bool wide = p->storage == LBM_STORE_FP32 || p->storage == LBM_STORE_FP64;
-  return p->kernel == LBM_KERNEL_TILED || (p->kernel == LBM_KERNEL_AUTO && wide);
+  return p->kernel == LBM_KERNEL_TILED || p->kernel == LBM_KERNEL_TMA || (p->kernel == LBM_KERNEL_AUTO && wide);
 }
+
+// Whether the TMA variant of the tiled schedule runs (FP32 storage).
+bool uses_tma(const lbm_params* p) { return p->kernel == LBM_KERNEL_TMA && p->storage == LBM_STORE_FP32; }
 
 // Whether a context keeps the per-tile lists of the halo schedule (4- and
 // 8-byte storage; 16-bit storage runs the two-pass schedule instead).
@@ -61,7 +64,8 @@ bool uses_halo(const lbm_params* p) {
 // The tiled schedule with 16-bit storage keeps a third density plane: a step
 // reads the encoding references rho(t - 1) and rho(t) and writes rho(t + 1).
 bool tiled16(const lbm_params* p) {
-  return p->kernel == LBM_KERNEL_TILED && (p->storage == LBM_STORE_FP16 || p->storage == LBM_STORE_BF16);
+  return (p->kernel == LBM_KERNEL_TILED || p->kernel == LBM_KERNEL_TMA) &&
+         (p->storage == LBM_STORE_FP16 || p->storage == LBM_STORE_BF16);
 }
 
 constexpr int MASS_BLOCKS = 1024;
@@ -76,6 +80,7 @@ bool layout(const lbm_params* p, const Geo& g, Layout* L) {
   size_t off = 0;
   L->f = off;        off = align_up(off + 2 * 18 * (size_t)g.plane * es, A);
   L->P = off;        off = align_up(off + (tiled16(p) ? 6 : 4) * (size_t)g.plane * cs, A);
+  L->U = off;        off = align_up(off + (es == 2 && p->velocity_refs ? 2 * (size_t)g.plane * 4 : 0), A);
   L->flags = off;    off = align_up(off + (size_t)g.plane * 2, A);
   L->list = off;     off = align_up(off + (size_t)cap * 4, A);
   L->imask = off;    off = align_up(off + (size_t)cap * 4, A);
@@ -100,6 +105,54 @@ bool layout(const lbm_params* p, const Geo& g, Layout* L) {
   return true;
 }
 
+// cuTensorMapEncodeTiled, resolved through the runtime (no link against the
+// driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// Tensor maps of the TMA schedule: each population buffer as (2 px floats,
+// py rows, 9 planes) and each density plane as (2 px floats, py rows), both
+// with the (2 (TILE_W + 4), TILE_H + 4) box of one tile's window. Out-of-
+// range rows and columns of a window (beyond the padded grid) read as zero
+// and are never used.
+bool encode_tma_maps(lbm_ctx* c) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  const Geo& g = c->g;
+  for (int b = 0; b < 2; ++b) {
+    const cuuint64_t dimf[3] = {(cuuint64_t)2 * g.px, (cuuint64_t)g.py, 9};
+    const cuuint64_t strf[2] = {(cuuint64_t)8 * g.px, (cuuint64_t)8 * g.plane};
+    const cuuint32_t boxf[3] = {(cuuint32_t)TMA_BOX_X, (cuuint32_t)TMA_WH, 1};
+    const cuuint32_t ones[3] = {1, 1, 1};
+    if (enc(&c->tmap_f[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->f[b], dimf, strf, boxf, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+    const cuuint64_t dimP[2] = {(cuuint64_t)2 * g.px, (cuuint64_t)g.py};
+    const cuuint64_t strP[1] = {(cuuint64_t)8 * g.px};
+    const cuuint32_t boxP[2] = {(cuuint32_t)TMA_BOX_X, (cuuint32_t)TMA_WH};
+    if (enc(&c->tmap_P[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->Pbuf[b], dimP, strP, boxP, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
 lbm_status fail(lbm_ctx* c, lbm_status s, const char* msg) {
   if (c) snprintf(c->err, sizeof(c->err), "%s", msg);
   return s;
@@ -109,6 +162,22 @@ lbm_status check_cuda(lbm_ctx* c, cudaError_t e, const char* where) {
   if (e == cudaSuccess) return LBM_OK;
   if (c) snprintf(c->err, sizeof(c->err), "%s: %s", where, cudaGetErrorString(e));
   return LBM_ERR_CUDA;
+}
+
+// The TMA schedule's bounded waits set small[4] when a copy was not seen to
+// complete; synchronising calls report it (and clear it).
+lbm_status check_timeout(lbm_ctx* c) {
+  if (!c->tma) return LBM_OK;
+  int v = 0;
+  lbm_status s = check_cuda(c, cudaMemcpyAsync(&v, c->small + 4, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                            "cudaMemcpyAsync");
+  if (!s) s = check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (s) return s;
+  if (v) {
+    s = check_cuda(c, cudaMemsetAsync(c->small + 4, 0, sizeof(int), c->stream), "cudaMemsetAsync");
+    return s ? s : fail(c, LBM_ERR_TIMEOUT, "a TMA copy of the tiled step did not complete within its bounded wait");
+  }
+  return LBM_OK;
 }
 
 lbm_status after_launch(lbm_ctx* c, const char* where) {
@@ -142,7 +211,8 @@ lbm_status launch_density_and_virtual(lbm_ctx* c, const T* f) {
   C* P = (C*)c->Pbuf[c->pcur ^ 1];
   const C* Pref = (const C*)c->Pbuf[c->pcur];
   lbm_status s = launch(c, LBM_KC_DENSITY, "k_density", [&] {
-    k_density<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>(f, P, Pref, c->flags, c->g, kphys<C>(c->ph));
+    k_density<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>(f, P, Pref, c->Ubuf[c->cur], c->flags, c->g,
+                                                                kphys<C>(c->ph));
   });
   if (s) return s;
   c->p_valid = false;
@@ -169,7 +239,7 @@ lbm_status step_two_pass(lbm_ctx* c, int nsteps) {
     C* P = (C*)c->Pbuf[c->pcur ^ 1];
     const C* Pref = (const C*)c->Pbuf[c->pcur];
     lbm_status s = launch(c, LBM_KC_DENSITY, "k_density_list", [&] {
-      k_density_list<T><<<nb, 256, 0, c->stream>>>(fin, P, Pref, c->flags, c->fluid_list, c->n_fluid, c->g,
+      k_density_list<T><<<nb, 256, 0, c->stream>>>(fin, P, Pref, c->Ubuf[c->cur], c->flags, c->fluid_list, c->n_fluid, c->g,
                                                   kphys<C>(c->ph));
     });
     if (s) return s;
@@ -181,7 +251,8 @@ lbm_status step_two_pass(lbm_ctx* c, int nsteps) {
       if (s) return s;
     }
     s = launch(c, LBM_KC_COLLIDE, "k_collide_list", [&] {
-      k_collide_list<T><<<nbc, COLLIDE_THREADS, 0, c->stream>>>(fin, fout, P, Pref, c->flags, c->fluid_list,
+      k_collide_list<T><<<nbc, COLLIDE_THREADS, 0, c->stream>>>(fin, fout, P, Pref, c->Ubuf[c->cur],
+                                                                c->Ubuf[c->cur ^ 1], c->flags, c->fluid_list,
                                                                 c->n_fluid, c->g, kphys<C>(c->ph));
     });
     if (s) return s;
@@ -200,7 +271,7 @@ lbm_status step_fused(lbm_ctx* c, int nsteps) {
     // rho of the current state, once; every fused step then produces the next
     lbm_status s = launch(c, LBM_KC_DENSITY, "k_density", [&] {
       k_density<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>((const T*)c->f[c->cur], (C*)c->P, (const C*)c->P,
-                                                                  c->flags, c->g, kphys<C>(c->ph));
+                                                                  nullptr, c->flags, c->g, kphys<C>(c->ph));
     });
     if (s) return s;
     c->p_valid = true;
@@ -220,9 +291,35 @@ lbm_status step_fused(lbm_ctx* c, int nsteps) {
       if (s) return s;
     }
     lbm_status ls = LBM_OK;
+    if constexpr (sizeof(T) == 4) {
+      if (c->tma) {
+        s = launch(c, LBM_KC_FUSED, "k_tile_tma", [&] {
+          constexpr size_t SMEM = tma_smem<T>();
+          if (!c->tma_smem_set) {
+            if (cudaFuncSetAttribute(k_tile_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM) !=
+                cudaSuccess) {
+              ls = LBM_ERR_CUDA;
+              return;
+            }
+            c->tma_smem_set = true;
+          }
+          const int ntx = (c->g.nx + TILE_W - 1) / TILE_W;
+          const int grid = (int)(c->n_tiles < c->num_sms ? c->n_tiles : c->num_sms);
+          k_tile_tma<<<grid, TMA_THREADS, SMEM, c->stream>>>(
+              c->tmap_f[c->cur], c->tmap_P[c->pcur], (float*)fout, (float*)Pout, c->flags, c->tile_entries,
+              c->tile_off, c->tile_nown, c->g, ntx, (int)c->n_tiles, kphys<float>(c->ph), c->small + 4);
+        });
+        if (ls) return fail(c, ls, "k_tile_tma launch rejected");
+        if (s) return s;
+        c->cur ^= 1;
+        c->pcur ^= 1;
+        c->P = c->Pbuf[c->pcur];
+        continue;
+      }
+    }
     if (c->n_tiles > 0) {
       s = launch(c, LBM_KC_FUSED, "k_tile", [&] {
-        ls = launch_tiled<T>(c->g, c->ph, fin, fout, Pin, Pin, Pout, c->flags, c->tile_entries, c->tile_off,
+        ls = launch_tiled<T>(c->g, c->ph, fin, fout, Pin, Pin, nullptr, nullptr, Pout, c->flags, c->tile_entries, c->tile_off,
                              c->tile_nown, &c->tile_smem_set, c->stream);
       });
     } else {
@@ -250,7 +347,8 @@ lbm_status step_tiled16(lbm_ctx* c, int nsteps) {
   if (nsteps > 0 && !c->p_valid) {
     lbm_status s = launch(c, LBM_KC_DENSITY, "k_density", [&] {
       k_density<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>((const T*)c->f[c->cur], (C*)c->Pbuf[c->pcur ^ 1],
-                                                                  (const C*)c->Pbuf[c->pcur], c->flags, c->g,
+                                                                  (const C*)c->Pbuf[c->pcur], c->Ubuf[c->cur],
+                                                                  c->flags, c->g,
                                                                   kphys<C>(c->ph));
     });
     if (s) return s;
@@ -272,7 +370,8 @@ lbm_status step_tiled16(lbm_ctx* c, int nsteps) {
     }
     lbm_status ls = LBM_OK;
     s = launch(c, LBM_KC_FUSED, "k_tile", [&] {
-      ls = launch_tiled<T>(c->g, c->ph, fin, fout, P, Pref, Po, c->flags, c->tile_entries, c->tile_off,
+      ls = launch_tiled<T>(c->g, c->ph, fin, fout, P, Pref, c->Ubuf[c->cur], c->Ubuf[c->cur ^ 1], Po, c->flags,
+                           c->tile_entries, c->tile_off,
                            c->tile_nown, &c->tile_smem_set, c->stream);
     });
     if (ls) return fail(c, ls, "tiled kernel launch rejected");
@@ -314,7 +413,7 @@ lbm_status do_step(lbm_ctx* c, int nsteps) {
   if constexpr (sizeof(T) >= 4) {  // the marching kernel stores 4- and 8-byte populations only
     if (c->n_halo_tiles > 0) return step_halo<T>(c, nsteps);
     if (c->prm.kernel == LBM_KERNEL_FUSED && fused_supported<T>(c->g, c->ph)) return step_fused<T>(c, nsteps);
-    const bool tiled = c->prm.kernel == LBM_KERNEL_TILED || c->prm.kernel == LBM_KERNEL_AUTO;
+    const bool tiled = c->prm.kernel == LBM_KERNEL_TILED || c->prm.kernel == LBM_KERNEL_AUTO || c->prm.kernel == LBM_KERNEL_TMA;
     if (tiled && c->n_tiles > 0) return step_fused<T>(c, nsteps);
   } else {
     if (c->Pbuf[2] && c->n_tiles > 0) return step_tiled16<T>(c, nsteps);
@@ -322,14 +421,15 @@ lbm_status do_step(lbm_ctx* c, int nsteps) {
   return step_two_pass<T>(c, nsteps);
 }
 
-template <typename T, int MODE>
-lbm_status do_eval(lbm_ctx* c, double* out) {
+template <typename T, int MODE, typename O = double>
+lbm_status do_eval(lbm_ctx* c, O* out) {
   const T* fin = (const T*)c->f[c->cur];
   lbm_status s = launch_density_and_virtual<T>(c, fin);
   if (s) return s;
   using C = typename Pop<T>::C;
-  k_collide<T, MODE><<<node_grid(c->g, 128), 128, 0, c->stream>>>(
-      fin, nullptr, (const C*)c->Pbuf[c->pcur ^ 1], (const C*)c->Pbuf[c->pcur], c->flags, c->g, kphys<C>(c->ph), out);
+  k_collide<T, MODE, O><<<node_grid(c->g, 128), 128, 0, c->stream>>>(
+      fin, (const C*)c->Pbuf[c->pcur ^ 1], (const C*)c->Pbuf[c->pcur], c->Ubuf[c->cur], c->flags, c->g,
+      kphys<C>(c->ph), out);
   return after_launch(c, "k_collide(eval)");
 }
 
@@ -337,6 +437,7 @@ template <typename T>
 lbm_status do_get_pops(lbm_ctx* c, double* out) {
   using C = typename Pop<T>::C;
   k_get_populations<T><<<node_grid(c->g, 128), 128, 0, c->stream>>>((const T*)c->f[c->cur], (const C*)c->P,
+                                                                     c->Ubuf[c->cur],
                                                                      c->flags, c->g, kphys<C>(c->ph), out);
   return after_launch(c, "k_get_populations");
 }
@@ -345,7 +446,8 @@ template <typename T, int SRC>
 lbm_status do_set_state(lbm_ctx* c, const double* fin, const double* rA, const double* rB, const double* ux,
                         const double* uy) {
   using C = typename Pop<T>::C;
-  k_set_state<T, SRC><<<node_grid(c->g, 128), 128, 0, c->stream>>>((T*)c->f[c->cur], (C*)c->P, c->flags, c->g,
+  k_set_state<T, SRC><<<node_grid(c->g, 128), 128, 0, c->stream>>>((T*)c->f[c->cur], (C*)c->P, c->Ubuf[c->cur],
+                                                                     c->flags, c->g,
                                                                      kphys<C>(c->ph), fin, rA, rB, ux, uy);
   return after_launch(c, "k_set_state");
 }
@@ -353,7 +455,8 @@ lbm_status do_set_state(lbm_ctx* c, const double* fin, const double* rA, const d
 template <typename T>
 lbm_status do_mass(lbm_ctx* c) {
   using C = typename Pop<T>::C;
-  k_mass_partial<T><<<c->mass_blocks, 256, 0, c->stream>>>((const T*)c->f[c->cur], (const C*)c->P, c->flags,
+  k_mass_partial<T><<<c->mass_blocks, 256, 0, c->stream>>>((const T*)c->f[c->cur], (const C*)c->P,
+                                                           c->Ubuf[c->cur], c->flags,
                                                            c->g, kphys<C>(c->ph), c->partial);
   lbm_status s = after_launch(c, "k_mass_partial");
   if (s) return s;
@@ -375,8 +478,9 @@ bool valid_params(const lbm_params* p) {
   if (p->nx < 4 || p->ny < 4) return false;
   if (!(p->tau[0] > 0.5) || !(p->tau[1] > 0.5)) return false;
   if (p->storage < LBM_STORE_FP32 || p->storage > LBM_STORE_BF16) return false;
-  if (p->kernel < LBM_KERNEL_AUTO || p->kernel > LBM_KERNEL_HALO) return false;
+  if (p->kernel < LBM_KERNEL_AUTO || p->kernel > LBM_KERNEL_TMA) return false;
   if (p->max_interface < 0) return false;
+  if (p->velocity_refs != 0 && p->velocity_refs != 1) return false;
   return true;
 }
 
@@ -436,6 +540,9 @@ lbm_status lbm_create(const lbm_params* params, void* d_workspace, size_t bytes,
   c->Pbuf[1] = c->ws + L.P + 2 * (size_t)g.plane * compute_size(params->storage);
   c->Pbuf[2] = tiled16(params) ? c->ws + L.P + 4 * (size_t)g.plane * compute_size(params->storage) : nullptr;
   c->Pbase = c->ws + L.P;
+  const bool uplanes = es == 2 && params->velocity_refs;
+  c->Ubuf[0] = uplanes ? (__half2*)(c->ws + L.U) : nullptr;
+  c->Ubuf[1] = uplanes ? (__half2*)(c->ws + L.U + (size_t)g.plane * 4) : nullptr;
   c->pcur = 0;
   c->P = c->Pbuf[0];
   c->p_valid = false;
@@ -444,6 +551,7 @@ lbm_status lbm_create(const lbm_params* params, void* d_workspace, size_t bytes,
   c->iface_mask = (uint32_t*)(c->ws + L.imask);
   c->fluid_list = (int*)(c->ws + L.flist);
   c->n_tiles = uses_tiles(params) ? tile_count(g) : 0;
+  c->tma = uses_tma(params);
   c->tile_entries = c->n_tiles ? (uint16_t*)(c->ws + L.tent) : nullptr;
   c->tile_off = c->n_tiles ? (int*)(c->ws + L.toff) : nullptr;
   c->tile_nown = c->n_tiles ? (int*)(c->ws + L.tnown) : nullptr;
@@ -478,6 +586,7 @@ lbm_status lbm_create(const lbm_params* params, void* d_workspace, size_t bytes,
   if (!s) s = check_cuda(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device),
                          "cudaDeviceGetAttribute");
   if (!s) s = check_cuda(c, cudaMemsetAsync(c->ws, 0, L.total, c->stream), "cudaMemsetAsync");
+  if (!s && c->tma && !encode_tma_maps(c)) s = LBM_ERR_CUDA;
   if (s) {
     delete c;
     return s;
@@ -581,6 +690,8 @@ lbm_status lbm_set_wetting(lbm_ctx* c, const lbm_wetting_params* w) {
     c->ph.chi[s] = w->chi[s];
     c->ph.rho_s[s] = w->rho_s[s];
   }
+  c->ph.uniform = w->kind == LBM_WET_VIRTUAL_AVG && w->pairing == LBM_PAIR_CROSS && w->G_s[0] == c->ph.G_AB &&
+                  w->G_s[1] == c->ph.G_AB;
   c->has_wetting = true;
   return LBM_OK;
 }
@@ -656,6 +767,7 @@ lbm_status lbm_step_profiled(lbm_ctx* c, int32_t nsteps, double* h_ms, int64_t* 
   c->prof_ev = nullptr;
   c->prof_cls = nullptr;
   c->prof_n = c->prof_cap = 0;
+  if (!s) s = check_timeout(c);
   if (s) return s;
   for (int k = 0; k < LBM_KC_COUNT; ++k) {
     if (h_ms) h_ms[k] = ms[k];
@@ -704,6 +816,7 @@ lbm_status lbm_mass(lbm_ctx* c, double* h_out) {
   if (s) return s;
   s = check_cuda(c, cudaMemcpyAsync(h_out, c->mass_out, 16, cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
   if (!s) s = check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (!s) s = check_timeout(c);
   return s;
 }
 
@@ -823,7 +936,8 @@ lbm_status lbm_interface_count(lbm_ctx* c, int64_t* n) {
 
 lbm_status lbm_sync(lbm_ctx* c) {
   if (!c) return LBM_ERR_ARG;
-  return check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  lbm_status s = check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  return s ? s : check_timeout(c);
 }
 
 lbm_status lbm_run_host(lbm_ctx* c, const lbm_wetting_params* w, const uint8_t* h_mask, const double* h_rhoA,
@@ -845,6 +959,38 @@ lbm_status lbm_run_host(lbm_ctx* c, const lbm_wetting_params* w, const uint8_t* 
   for (int a = 0; a < 4 && !s; ++a)
     if (outs[a])
       s = check_cuda(c, cudaMemcpyAsync(outs[a], c->stage + a * N, N * 8, cudaMemcpyDeviceToHost, c->stream),
+                     "cudaMemcpyAsync");
+  if (!s) s = check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  return s;
+}
+
+lbm_status lbm_run_host_f32(lbm_ctx* c, const lbm_wetting_params* w, const uint8_t* h_mask, const float* h_rhoA,
+                            const float* h_rhoB, int32_t nsteps, float* oA, float* oB, float* oux, float* ouy) {
+  if (!c || !w || !h_mask || !h_rhoA || !h_rhoB || nsteps < 0) return LBM_ERR_ARG;
+  const int64_t N = (int64_t)c->g.nx * c->g.ny;
+  // staging (4 N doubles): the FP32 inputs in its last quarter, widened to
+  // doubles in its first half; the FP32 moments later in its first half
+  float* in32 = reinterpret_cast<float*>(c->stage + 3 * N);
+  double* in = c->stage;
+  lbm_status s = check_cuda(c, cudaMemcpyAsync(c->stage_mask, h_mask, N, cudaMemcpyHostToDevice, c->stream),
+                            "cudaMemcpyAsync");
+  if (!s) s = check_cuda(c, cudaMemcpyAsync(in32, h_rhoA, N * 4, cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync");
+  if (!s) s = check_cuda(c, cudaMemcpyAsync(in32 + N, h_rhoB, N * 4, cudaMemcpyHostToDevice, c->stream),
+                         "cudaMemcpyAsync");
+  if (s) return s;
+  k_widen<<<(unsigned)((2 * N + 255) / 256), 256, 0, c->stream>>>(in32, in, 2 * N);
+  if ((s = after_launch(c, "k_widen"))) return s;
+  s = lbm_set_geometry(c, c->stage_mask);
+  if (!s) s = lbm_set_wetting(c, w);
+  if (!s) s = lbm_init_fields(c, in, in + N, nullptr, nullptr);
+  if (!s) s = lbm_step(c, nsteps);
+  if (s) return s;
+  float* out = reinterpret_cast<float*>(c->stage);
+  LBM_DISPATCH(c, s = (do_eval<T, 1, float>(c, out)); break);
+  float* outs[4] = {oA, oB, oux, ouy};
+  for (int a = 0; a < 4 && !s; ++a)
+    if (outs[a])
+      s = check_cuda(c, cudaMemcpyAsync(outs[a], out + a * N, N * 4, cudaMemcpyDeviceToHost, c->stream),
                      "cudaMemcpyAsync");
   if (!s) s = check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   return s;

@@ -1,5 +1,9 @@
-// Batched stepping of many independent simulations (contexts) with one
-// launch per kernel class per step, replayed from a CUDA graph.
+// Batched stepping of many independent simulations (contexts): each step is
+// one launch per kernel class over all members, through block tables that
+// map a CTA to (member, first list entry) or (member, tile), replayed from
+// a CUDA graph. Two schedules, as for a single simulation: the two-pass one
+// (density pass, Eq. 8 pass, collide pass) and, for 4- and 8-byte storage
+// with tile lists, the tiled single pass (Eq. 8 pass, tiled step).
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -19,7 +23,12 @@ template <typename C>
 struct BatchDesc {
   const void* f[2];
   void* Pbuf[2];
+  __half2* Ubuf[2];  // 16-bit storage: velocity part of the references of f[0] / f[1]
   const uint16_t* flags;
+  const uint16_t* tile_entries;  // tiled schedule: the member's per-tile lists
+  const int* tile_off;
+  const int* tile_nown;
+  int n_tiles, ntx;
   const int* fluid_list;
   const int* iface_list;
   const uint32_t* iface_mask;
@@ -29,27 +38,45 @@ struct BatchDesc {
   PhysK<C> ph;
 };
 
+// Densities of the members' current populations. into: 1 into Pbuf[pcur ^ 1]
+// (two-pass: the plane the collide pass reads), 0 into Pbuf[pcur] (tiled:
+// rho(t) before the first tiled step; 4- and 8-byte storage).
 template <typename T>
 __global__ void __launch_bounds__(256) k_density_batch(const BatchDesc<typename Pop<T>::C>* __restrict__ d,
-                                                       const int2* __restrict__ blk, int parity) {
+                                                       const int2* __restrict__ blk, int parity, int into) {
   using C = typename Pop<T>::C;
   const int2 b = blk[blockIdx.x];
   const BatchDesc<C>& D = d[b.x];
   const int cur = D.cur ^ parity, pcur = D.pcur ^ parity;
   const int t = b.y + threadIdx.x;
   if (t < D.n_fluid)
-    density_node<T>((const T*)D.f[cur], (C*)D.Pbuf[pcur ^ 1], (const C*)D.Pbuf[pcur], D.flags, D.fluid_list, t,
-                    D.g);
+    density_node<T>((const T*)D.f[cur], (C*)D.Pbuf[pcur ^ into], (const C*)D.Pbuf[pcur], D.Ubuf[cur], D.flags,
+                    D.fluid_list, t, D.g);
 }
 
+// Eq. 8 into the plane the next pass reads: Pbuf[pcur ^ into] (into as
+// above).
 template <typename C>
 __global__ void __launch_bounds__(128) k_virtual_batch(const BatchDesc<C>* __restrict__ d,
-                                                       const int2* __restrict__ blk, int parity) {
+                                                       const int2* __restrict__ blk, int parity, int into) {
   const int2 b = blk[blockIdx.x];
   const BatchDesc<C>& D = d[b.x];
   const int pcur = D.pcur ^ parity;
   const int t = b.y + threadIdx.x;
-  if (t < D.n_iface) virtual_density_node<C>((C*)D.Pbuf[pcur ^ 1], D.iface_mask, D.iface_list, t, D.g, D.ph);
+  if (t < D.n_iface) virtual_density_node<C>((C*)D.Pbuf[pcur ^ into], D.iface_mask, D.iface_list, t, D.g, D.ph);
+}
+
+// Tiled single-pass step of every member: CTA -> (member, tile).
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS, TILE_MINB)
+    k_tile_batch(const BatchDesc<typename Pop<T>::C>* __restrict__ d, const int2* __restrict__ blk, int parity) {
+  using C = typename Pop<T>::C;
+  const int2 b = blk[blockIdx.x];
+  const BatchDesc<C>& D = d[b.x];
+  const int cur = D.cur ^ parity, pcur = D.pcur ^ parity;
+  tile_step<T>(b.y, D.n_tiles, (const T*)D.f[cur], (T*)D.f[cur ^ 1], (const C*)D.Pbuf[pcur],
+               (const C*)D.Pbuf[pcur], nullptr, nullptr, (C*)D.Pbuf[pcur ^ 1], D.flags, D.tile_entries,
+               D.tile_off, D.tile_nown, D.g, D.ntx, D.ph);
 }
 
 template <typename T>
@@ -59,8 +86,8 @@ __global__ void __launch_bounds__(256) k_collide_batch(const BatchDesc<typename 
   const int2 b = blk[blockIdx.x];
   const BatchDesc<C>& D = d[b.x];
   const int cur = D.cur ^ parity, pcur = D.pcur ^ parity;
-  collide_node<T>((const T*)D.f[cur], (T*)D.f[cur ^ 1], (const C*)D.Pbuf[pcur ^ 1], (const C*)D.Pbuf[pcur], D.flags,
-                  D.fluid_list, b.y + threadIdx.x, D.n_fluid, D.g, D.ph);
+  collide_node<T>((const T*)D.f[cur], (T*)D.f[cur ^ 1], (const C*)D.Pbuf[pcur ^ 1], (const C*)D.Pbuf[pcur],
+                  D.Ubuf[cur], D.Ubuf[cur ^ 1], D.flags, D.fluid_list, b.y + threadIdx.x, D.n_fluid, D.g, D.ph);
 }
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -87,7 +114,10 @@ struct lbm_batch {
   void* d_desc;
   int2* d_fblk;
   int2* d_iblk;
-  int n_fblk, n_iblk;
+  int2* d_tblk;         // tiled schedule: (member, tile) per CTA (null if unavailable)
+  int n_fblk, n_iblk, n_tblk;
+  int schedule;         // LBM_KERNEL_TWO_PASS or LBM_KERNEL_TILED
+  bool tiled_ok;        // 4- or 8-byte storage and every member keeps tile lists
   int bs;               // threads per block of the density and collide kernels
   void* h_desc;         // host staging of the descriptors
   int2* h_tab;          // host staging of the block tables
@@ -112,10 +142,19 @@ lbm_status bcuda(lbm_batch* b, cudaError_t e, const char* where) {
 }
 
 // Device layout of a batch workspace: descriptors, fluid block table (sized
-// for the smallest block size), interface block table.
+// for the smallest block size), interface block table, tile block table.
 struct BLayout {
-  size_t desc, fblk, iblk, total;
+  size_t desc, fblk, iblk, tblk, total;
 };
+
+// The tiled schedule runs when the storage is 4 or 8 bytes and every member
+// keeps the per-tile lists (contexts created with LBM_KERNEL_AUTO or TILED).
+bool batch_tiled_ok(int n, lbm_ctx* const* ctxs) {
+  if (ctxs[0]->prm.storage != LBM_STORE_FP32 && ctxs[0]->prm.storage != LBM_STORE_FP64) return false;
+  for (int s = 0; s < n; ++s)
+    if (ctxs[s]->n_tiles <= 0) return false;
+  return true;
+}
 
 BLayout blayout(int n, lbm_ctx* const* ctxs) {
   int* lf = (int*)malloc(sizeof(int) * n);
@@ -129,6 +168,10 @@ BLayout blayout(int n, lbm_ctx* const* ctxs) {
   L.desc = off;  off = align_up(off + (size_t)n * desc_bytes(ctxs[0]->prm.storage), 256);
   L.fblk = off;  off = align_up(off + (size_t)table_entries(lf, n, 128) * sizeof(int2), 256);
   L.iblk = off;  off = align_up(off + (size_t)table_entries(li, n, 128) * sizeof(int2), 256);
+  int64_t nt = 0;
+  if (batch_tiled_ok(n, ctxs))
+    for (int s = 0; s < n; ++s) nt += ctxs[s]->n_tiles;
+  L.tblk = off;  off = align_up(off + (size_t)nt * sizeof(int2), 256);
   L.total = off;
   free(lf);
   free(li);
@@ -163,7 +206,14 @@ void fill_descs(lbm_batch* b) {
     d.f[1] = c->f[1];
     d.Pbuf[0] = c->Pbuf[0];
     d.Pbuf[1] = c->Pbuf[1];
+    d.Ubuf[0] = c->Ubuf[0];
+    d.Ubuf[1] = c->Ubuf[1];
     d.flags = c->flags;
+    d.tile_entries = c->tile_entries;
+    d.tile_off = c->tile_off;
+    d.tile_nown = c->tile_nown;
+    d.n_tiles = (int)c->n_tiles;
+    d.ntx = (c->g.nx + TILE_W - 1) / TILE_W;
     d.fluid_list = c->fluid_list;
     d.iface_list = c->iface_list;
     d.iface_mask = c->iface_mask;
@@ -181,12 +231,25 @@ template <typename T>
 lbm_status launch_step(lbm_batch* b, int p) {
   using C = typename Pop<T>::C;
   const BatchDesc<C>* d = (const BatchDesc<C>*)b->d_desc;
+  if (b->schedule == LBM_KERNEL_TILED) {
+    if constexpr (sizeof(T) >= 4) {
+      if (b->n_iblk > 0) {
+        k_virtual_batch<C><<<b->n_iblk, 128, 0, b->stream>>>(d, b->d_iblk, p, 0);
+        b->launches++;
+      }
+      if (b->n_tblk > 0) {
+        k_tile_batch<T><<<b->n_tblk, TILE_THREADS, tile_smem<T>(), b->stream>>>(d, b->d_tblk, p);
+        b->launches++;
+      }
+    }
+    return bcuda(b, cudaGetLastError(), "batched tiled step launch");
+  }
   if (b->n_fblk > 0) {
-    k_density_batch<T><<<b->n_fblk, b->bs, 0, b->stream>>>(d, b->d_fblk, p);
+    k_density_batch<T><<<b->n_fblk, b->bs, 0, b->stream>>>(d, b->d_fblk, p, 1);
     b->launches++;
   }
   if (b->n_iblk > 0) {
-    k_virtual_batch<C><<<b->n_iblk, 128, 0, b->stream>>>(d, b->d_iblk, p);
+    k_virtual_batch<C><<<b->n_iblk, 128, 0, b->stream>>>(d, b->d_iblk, p, 1);
     b->launches++;
   }
   if (b->n_fblk > 0) {
@@ -194,6 +257,12 @@ lbm_status launch_step(lbm_batch* b, int p) {
     b->launches++;
   }
   return bcuda(b, cudaGetLastError(), "batched step launch");
+}
+
+// Kernel launches per step of the current schedule.
+int launches_per_step(const lbm_batch* b) {
+  if (b->schedule == LBM_KERNEL_TILED) return (b->n_iblk > 0) + (b->n_tblk > 0);
+  return (b->n_fblk > 0) * 2 + (b->n_iblk > 0);
 }
 
 void drop_graph(lbm_batch* b) {
@@ -214,22 +283,28 @@ lbm_status build_graph(lbm_batch* b, int steps) {
   if (st) return st;
   const BatchDesc<C>* d = (const BatchDesc<C>*)b->d_desc;
   cudaGraphNode_t prev = nullptr;
+  const bool tiled = b->schedule == LBM_KERNEL_TILED;
+  void* tile_fn = nullptr;
+  if constexpr (sizeof(T) >= 4) tile_fn = (void*)k_tile_batch<T>;
   for (int k = 0; k < steps && !st; ++k) {
     int p = k & 1;
-    const int2* tabs[3] = {b->d_fblk, b->d_iblk, b->d_fblk};
-    void* fns[3] = {(void*)k_density_batch<T>, (void*)k_virtual_batch<C>, (void*)k_collide_batch<T>};
-    const int grids[3] = {b->n_fblk, b->n_iblk, b->n_fblk};
-    const int blocks[3] = {b->bs, 128, b->bs};
+    int into = tiled ? 0 : 1;
+    const int2* tabs[3] = {b->d_fblk, b->d_iblk, tiled ? b->d_tblk : b->d_fblk};
+    void* fns[3] = {(void*)k_density_batch<T>, (void*)k_virtual_batch<C>,
+                    tiled ? tile_fn : (void*)k_collide_batch<T>};
+    const int grids[3] = {tiled ? 0 : b->n_fblk, b->n_iblk, tiled ? b->n_tblk : b->n_fblk};
+    const int blocks[3] = {b->bs, 128, tiled ? TILE_THREADS : b->bs};
+    const size_t smem[3] = {0, 0, tiled ? tile_smem<T>() : 0};
     for (int q = 0; q < 3 && !st; ++q) {
       if (grids[q] <= 0) continue;
       const int2* tab = tabs[q];
-      void* args[3] = {(void*)&d, (void*)&tab, (void*)&p};
+      void* args[4] = {(void*)&d, (void*)&tab, (void*)&p, (void*)&into};
       cudaKernelNodeParams kp;
       memset(&kp, 0, sizeof(kp));
       kp.func = fns[q];
       kp.gridDim = dim3(grids[q]);
       kp.blockDim = dim3(blocks[q]);
-      kp.sharedMemBytes = 0;
+      kp.sharedMemBytes = (unsigned)smem[q];
       kp.kernelParams = args;
       cudaGraphNode_t node;
       st = bcuda(b, cudaGraphAddKernelNode(&node, b->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp),
@@ -254,11 +329,23 @@ lbm_status batch_step(lbm_batch* b, int nsteps) {
                                            cudaMemcpyHostToDevice, b->stream), "cudaMemcpyAsync");
   // the staging buffer is rewritten by the next call: wait for the copy
   if (!st) st = bcuda(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+  const bool tiled = b->schedule == LBM_KERNEL_TILED;
+  if (!st && tiled && nsteps > 0) {
+    // the tiled step reads rho(t) from Pbuf[pcur]: compute it for every
+    // member once (a member whose plane already holds it gets the same bits)
+    bool all_valid = true;
+    for (int s = 0; s < b->n; ++s) all_valid = all_valid && b->ctx[s]->p_valid;
+    if (!all_valid && b->n_fblk > 0) {
+      k_density_batch<T><<<b->n_fblk, b->bs, 0, b->stream>>>((const BatchDesc<C>*)b->d_desc, b->d_fblk, 0, 0);
+      b->launches++;
+      st = bcuda(b, cudaGetLastError(), "batched density launch");
+    }
+  }
   int done = 0;
   if (b->exec && b->graph_steps > 0)
     for (; !st && done + b->graph_steps <= nsteps; done += b->graph_steps) {
       st = bcuda(b, cudaGraphLaunch(b->exec, b->stream), "cudaGraphLaunch");
-      b->launches += (int64_t)b->graph_steps * ((b->n_fblk > 0) * 2 + (b->n_iblk > 0));
+      b->launches += (int64_t)b->graph_steps * launches_per_step(b);
     }
   for (; !st && done < nsteps; ++done) st = launch_step<T>(b, done & 1);
   if (st) return st;
@@ -269,7 +356,8 @@ lbm_status batch_step(lbm_batch* b, int nsteps) {
       c->pcur ^= 1;
       c->P = c->Pbuf[c->pcur];
     }
-    c->p_valid = false;
+    // after tiled steps Pbuf[pcur] holds rho of the current state
+    c->p_valid = tiled && (nsteps > 0 || c->p_valid);
   }
   return LBM_OK;
 }
@@ -323,17 +411,22 @@ lbm_status lbm_batch_create(int32_t n, lbm_ctx* const* ctxs, void* d_workspace, 
   b->d_desc = b->ws + L.desc;
   b->d_fblk = (int2*)(b->ws + L.fblk);
   b->d_iblk = (int2*)(b->ws + L.iblk);
+  b->tiled_ok = batch_tiled_ok(n, ctxs);
+  b->d_tblk = b->tiled_ok ? (int2*)(b->ws + L.tblk) : nullptr;
+  b->schedule = LBM_KERNEL_TWO_PASS;
   b->ctx = (lbm_ctx**)malloc(sizeof(lbm_ctx*) * n);
   b->h_desc = malloc((size_t)n * desc_bytes(b->storage));
-  // host staging large enough for either table at 128 threads per block
+  // host staging large enough for any table (fluid and interface tables at
+  // 128 threads per block, the tile table)
   int64_t tab_cap = 1;
   {
-    int64_t ef = 0, ei = 0;
+    int64_t ef = 0, ei = 0, et = 0;
     for (int s = 0; s < n; ++s) {
       ef += (ctxs[s]->n_fluid + 127) / 128;
       ei += ctxs[s]->ph.bc == BC_VAVG ? (ctxs[s]->n_iface + 127) / 128 : 0;
+      et += b->tiled_ok ? ctxs[s]->n_tiles : 0;
     }
-    tab_cap += ef > ei ? ef : ei;
+    tab_cap += ef > ei ? (ef > et ? ef : et) : (ei > et ? ei : et);
   }
   b->h_tab = (int2*)malloc((size_t)tab_cap * sizeof(int2));
   if (!b->ctx || !b->h_desc || !b->h_tab) {
@@ -352,6 +445,19 @@ lbm_status lbm_batch_create(int32_t n, lbm_ctx* const* ctxs, void* d_workspace, 
                                 b->stream), "cudaMemcpyAsync");
   if (!st) st = bcuda(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
   if (!st) st = upload_fluid_table(b, 256);
+  if (!st && b->tiled_ok) {
+    // tile blocks: every tile of every member, member by member
+    int e = 0;
+    for (int s = 0; s < n; ++s)
+      for (int64_t t = 0; t < b->ctx[s]->n_tiles; ++t) b->h_tab[e++] = make_int2(s, (int)t);
+    b->n_tblk = e;
+    st = bcuda(b, cudaMemcpyAsync(b->d_tblk, b->h_tab, (size_t)e * sizeof(int2), cudaMemcpyHostToDevice, b->stream),
+               "cudaMemcpyAsync");
+    if (!st) st = bcuda(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    if (!st && b->storage == LBM_STORE_FP64)
+      st = bcuda(b, cudaFuncSetAttribute(k_tile_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tile_smem<double>()), "cudaFuncSetAttribute");
+  }
   if (st) {
     free(b->ctx);
     free(b->h_desc);
@@ -379,9 +485,29 @@ lbm_status lbm_batch_step(lbm_batch* b, int32_t nsteps) {
   return st;
 }
 
+lbm_status lbm_batch_set_schedule(lbm_batch* b, int32_t kernel) {
+  if (!b) return LBM_ERR_ARG;
+  if (kernel != LBM_KERNEL_TWO_PASS && kernel != LBM_KERNEL_TILED) return bfail(b, LBM_ERR_ARG, "unknown schedule");
+  if (kernel == LBM_KERNEL_TILED && !b->tiled_ok)
+    return bfail(b, LBM_ERR_ARG, "tiled schedule needs 4- or 8-byte storage and members with tile lists");
+  b->schedule = kernel;
+  return b->graph_steps > 0 ? lbm_batch_set_graph_steps(b, b->graph_steps) : LBM_OK;
+}
+
+lbm_status lbm_batch_config(const lbm_batch* b, int32_t* h_cfg) {
+  if (!b || !h_cfg) return LBM_ERR_ARG;
+  h_cfg[0] = b->schedule;
+  h_cfg[1] = b->schedule == LBM_KERNEL_TILED ? TILE_THREADS : b->bs;
+  h_cfg[2] = b->graph_steps;
+  return LBM_OK;
+}
+
 lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, int32_t* h_choice) {
   if (!b || trial_steps < 2) return LBM_ERR_ARG;
-  static const int kBs[2] = {128, 256};
+  // candidates: the two-pass schedule at 128 or 256 threads per block, and
+  // the tiled one when available; 2, 8 or 32 steps per graph replay
+  struct Cand { int schedule, bs; };
+  const Cand kCand[3] = {{LBM_KERNEL_TWO_PASS, 128}, {LBM_KERNEL_TWO_PASS, 256}, {LBM_KERNEL_TILED, 256}};
   static const int kSteps[3] = {2, 8, 32};
   cudaEvent_t e0, e1;
   lbm_status st = bcuda(b, cudaEventCreate(&e0), "cudaEventCreate");
@@ -392,9 +518,12 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, int32_t* h_choi
     return st;
   }
   float best = 1e30f;
-  int best_bs = 256, best_steps = 2;
-  for (int ib = 0; ib < 2 && !st; ++ib) {
-    st = upload_fluid_table(b, kBs[ib]);
+  Cand best_c = kCand[1];
+  int best_steps = 2;
+  for (int ic = 0; ic < 3 && !st; ++ic) {
+    if (kCand[ic].schedule == LBM_KERNEL_TILED && !b->tiled_ok) continue;
+    st = upload_fluid_table(b, kCand[ic].bs);
+    if (!st) st = lbm_batch_set_schedule(b, kCand[ic].schedule);
     for (int is = 0; is < 3 && !st; ++is) {
       const int S = kSteps[is];
       st = lbm_batch_set_graph_steps(b, S);
@@ -408,17 +537,18 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, int32_t* h_choi
       if (!st) st = bcuda(b, cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
       if (!st && ms / (reps * S) < best) {
         best = ms / (reps * S);
-        best_bs = kBs[ib];
+        best_c = kCand[ic];
         best_steps = S;
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (!st) st = upload_fluid_table(b, best_bs);
+  if (!st) st = upload_fluid_table(b, best_c.bs);
+  if (!st) st = lbm_batch_set_schedule(b, best_c.schedule);
   if (!st) st = lbm_batch_set_graph_steps(b, best_steps);
   if (!st && h_choice) {
-    h_choice[0] = best_bs;
+    h_choice[0] = best_c.schedule == LBM_KERNEL_TILED ? TILE_THREADS : best_c.bs;
     h_choice[1] = best_steps;
   }
   return st;

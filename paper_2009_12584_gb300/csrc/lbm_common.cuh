@@ -221,6 +221,11 @@ struct Phys {
   double rho_s[2];   // constant solid densities
   double rho_ref[2]; // FP16/BF16 storage reference densities
   int bc, pairing, avg9;
+  // Eq. 7 with the improved scheme's virtual densities, cross pairing and
+  // G_As = G_Bs = G_AB: the solid neighbours then enter exactly like fluid
+  // ones (the density plane holds rho~ there), so every node can take the
+  // one-sum formula of a node without solid neighbours
+  int uniform;
 };
 
 // The same constants in the arithmetic type of a kernel, converted once on
@@ -228,7 +233,7 @@ struct Phys {
 template <typename C>
 struct PhysK {
   C omega[2], kF[2], G_AB, G_s[2], chi[2], rho_s[2], rho_ref[2];
-  int bc, pairing, avg9;
+  int bc, pairing, avg9, uniform;
 };
 
 template <typename C>
@@ -246,6 +251,7 @@ inline PhysK<C> kphys(const Phys& p) {
   k.bc = p.bc;
   k.pairing = p.pairing;
   k.avg9 = p.avg9;
+  k.uniform = p.uniform;
   return k;
 }
 
@@ -266,12 +272,13 @@ __device__ __forceinline__ void weighted_sum(const C q[9], C& sx, C& sy) {
 // know their whole warp is bulk pass fl = 0; others pass false so that a
 // warp does not split between the two paths). The general path splits the
 // neighbour values by select into a fluid and a solid part and sums each
-// with the bulk formula.
+// with the bulk formula. With ph.uniform (see Phys) every node takes the
+// short path.
 template <typename C, bool BULK_FAST = true>
 __device__ __forceinline__ void interaction_force(const PhysK<C>& ph, uint16_t fl, const C rho[2],
                                                   const C nbP[2][9], C F[2][2]) {
   const C G = ph.G_AB;
-  if (BULK_FAST && !(fl & NB_ANY)) {
+  if ((BULK_FAST && !(fl & NB_ANY)) || ph.uniform) {
     // bulk node: every neighbour is fluid, Eq. 5 over all eight
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
@@ -410,7 +417,8 @@ __device__ __forceinline__ void collide(C f[2][9], const C rho[2], C ux, C uy, c
 // fluid node x is solid, what x receives along c_i at the next step is its
 // own post-collision f*_opp(i) (Sec. 2); it is stored in slot i of that solid
 // node (and its periodic images), which no other node writes, so that every
-// pull reads f*_i(x - c_i) without a test.
+// pull reads f*_i(x - c_i) without a test. ref[s][d] is the encoding
+// reference of the node's value along c_d, so slot i takes ref[s][opp(i)].
 template <typename T, typename C>
 __device__ __forceinline__ void store_bounced(T* __restrict__ fo, const Geo& g, int x, int y, uint16_t fl,
                                               const C fv[2][9], const C ref[2][9]) {
@@ -422,7 +430,7 @@ __device__ __forceinline__ void store_bounced(T* __restrict__ fo, const Geo& g, 
     if (g.per_x) sx = (sx + g.nx) % g.nx;
     if (g.per_y) sy = (sy + g.ny) % g.ny;
     const int ks = g.idx(sx, sy);
-    const C a = fv[0][opp_of(i)], b = fv[1][opp_of(i)], ra = ref[0][i], rb = ref[1][i];
+    const C a = fv[0][opp_of(i)], b = fv[1][opp_of(i)], ra = ref[0][opp_of(i)], rb = ref[1][opp_of(i)];
     Pop<T>::st2(fo, pslot(g, i, ks), a, b, ra, rb);
     for_ghost_images(g, sx, sy, [&](int kk) { Pop<T>::st2(fo, pslot(g, i, kk), a, b, ra, rb); });
   }
@@ -438,7 +446,7 @@ __device__ __forceinline__ void store_bounced_near(T* __restrict__ fo, const Geo
   for (int i = 1; i < 9; ++i) {
     if (!(fl & nb_bit(opp_of(i)))) continue;
     const int ks = k - cx_of(i) - cy_of(i) * g.px;
-    Pop<T>::st2(fo, pslot(g, i, ks), fv[0][opp_of(i)], fv[1][opp_of(i)], ref[0][i], ref[1][i]);
+    Pop<T>::st2(fo, pslot(g, i, ks), fv[0][opp_of(i)], fv[1][opp_of(i)], ref[0][opp_of(i)], ref[1][opp_of(i)]);
   }
 }
 

@@ -38,11 +38,11 @@ struct MarchCfg {
 
 // Force, velocity and collision of one fluid node in place (fv: f on entry,
 // f* on exit; nbP: density plane at x + c_i; rho: the node's densities on
-// exit). The FP32 compute type runs the paired path of the two-pass kernel
-// (same arithmetic, same results).
+// exit; u: the velocity of Eq. 3). The FP32 compute type runs the paired
+// path of the two-pass kernel (same arithmetic, same results).
 template <typename C>
 __device__ __forceinline__ void march_update(C fv[2][9], const C nbP[2][9], uint16_t fl, bool general,
-                                             const PhysK<C>& ph, C rho_out[2]) {
+                                             const PhysK<C>& ph, C rho_out[2], C u_out[2]) {
   if constexpr (sizeof(C) == 4) {
     float2 fp[9], q[9];
 #pragma unroll
@@ -50,7 +50,8 @@ __device__ __forceinline__ void march_update(C fv[2][9], const C nbP[2][9], uint
       fp[i] = f2(fv[0][i], fv[1][i]);
       q[i] = f2(nbP[0][i], nbP[1][i]);
     }
-    const float2 r = general ? update_pair<true>(fp, q, fl, ph) : update_pair<false>(fp, q, fl, ph);
+    const float2 r = general ? update_pair<true>(fp, q, fl, ph, u_out[0], u_out[1])
+                             : update_pair<false>(fp, q, fl, ph, u_out[0], u_out[1]);
     rho_out[0] = r.x;
     rho_out[1] = r.y;
 #pragma unroll
@@ -71,6 +72,8 @@ __device__ __forceinline__ void march_update(C fv[2][9], const C nbP[2][9], uint
     const C ux = ((jxA + jxB) + C(0.5) * (F[0][0] + F[1][0])) * inv;
     const C uy = ((jyA + jyB) + C(0.5) * (F[0][1] + F[1][1])) * inv;
     collide(fv, rho, ux, uy, F, ph.omega, ph.kF);
+    u_out[0] = ux;
+    u_out[1] = uy;
   }
 }
 
@@ -176,7 +179,8 @@ __global__ void __launch_bounds__(MARCH_WARPS * 32, 4)
     T* rrow = ring + (size_t)((y + MARCH_RING) % MARCH_RING) * 18 * 32 + lane;
     if (fluid) {
       C rho_unused[2];
-      march_update<C>(fv, nbP, fl, general, ph, rho_unused);
+      C u_unused[2];
+      march_update<C>(fv, nbP, fl, general, ph, rho_unused, u_unused);
 #pragma unroll
       for (int s = 0; s < 2; ++s)
 #pragma unroll

@@ -249,8 +249,8 @@ __global__ void __launch_bounds__(HALO_THREADS, HALO_MINB)
       nbP[0][i] = v.x;
       nbP[1][i] = v.y;
     }
-    C rh[2];
-    march_update<C>(fv, nbP, fl, warp_edge, ph, rh);
+    C rh[2], uu[2];
+    march_update<C>(fv, nbP, fl, warp_edge, ph, rh, uu);
     if (!warp_border) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) Pop<T>::st2(fo, pslot(g, i, k), fv[0][i], fv[1][i], C(0), C(0));

@@ -8,11 +8,19 @@
 #include "lbm_halo.cuh"
 #include "lbm_kernels.cuh"
 #include "lbm_tiled.cuh"
+#include "lbm_tma.cuh"
 
 using lbm::Geo;
 using lbm::Phys;
 
 struct lbm_ctx {
+  // TMA schedule: tensor maps of the population buffers f[0], f[1] (rank 3:
+  // 2 px floats, py rows, 9 planes) and the density planes Pbuf[0], Pbuf[1]
+  // (rank 2), encoded at creation
+  alignas(64) CUtensorMap tmap_f[2];
+  alignas(64) CUtensorMap tmap_P[2];
+  bool tma;            // the TMA schedule runs (FP32 storage, LBM_KERNEL_TMA)
+  bool tma_smem_set;   // k_tile_tma's dynamic shared memory limit raised
   lbm_params prm;
   Geo g;
   Phys ph;
@@ -26,6 +34,8 @@ struct lbm_ctx {
   void* Pbuf[3];       // density plane pairs (compute type); the third only for
                        // the tiled schedule with 16-bit storage (null otherwise)
   char* Pbase;         // start of the density planes in the workspace
+  __half2* Ubuf[2];    // 16-bit storage with velocity_refs: 3 u of the writers of f[0] / f[1] (the
+                       // velocity part of the encoding references); null otherwise
   void* P;             // Pbuf[pcur]: the densities the current populations were
                        // written with (16-bit encoding references); after a
                        // single-pass step, the densities of the current state

@@ -34,21 +34,44 @@ __device__ __forceinline__ void prefetch_list_ahead(const int* __restrict__ list
   }
 }
 
-// Encoding references of 16-bit storage. A 2-byte population is stored as
-// its deviation from w_i rho of the node that wrote it, rho being that
-// node's density when it collided (kept in the reference density plane
-// Pref): the deviation is the non-equilibrium and velocity part, a few
-// percent of f, so the 11 (FP16) or 8 (BF16) significand bits go to what
-// varies. For 4- and 8-byte storage the references are not used.
+// Encoding references of 16-bit storage. A 2-byte population travelling
+// along c_d is stored as its deviation from w_d rho (1 + c_d . U), the part
+// of its writer's equilibrium (Eq. 2) that is linear in u, with rho and
+// U = 3 u (rounded to FP16) of the node that wrote it, taken when it
+// collided. rho is kept in the reference density plane Pref and U in the
+// velocity plane Uref, so that the reader forms the same reference; the
+// deviation is then the non-equilibrium part and the O(u^2) terms, and the
+// 11 (FP16) or 8 (BF16) significand bits go to what varies. For 4- and
+// 8-byte storage the references are zero and the planes are not read.
 template <typename T>
 constexpr bool kDev = sizeof(T) == 2;
 
+// c_d . U as a fixed sequence of FP32 operations; for -c_d it gives the
+// exact negation (round to nearest is symmetric).
+__device__ __forceinline__ float cdot(int d, float2 U) {
+  const int cx = cx_of(d), cy = cy_of(d);
+  float v = cx > 0 ? U.x : (cx < 0 ? -U.x : 0.0f);
+  if (cy > 0) v = cx != 0 ? v + U.y : U.y;
+  if (cy < 0) v = cx != 0 ? v - U.y : -U.y;
+  return v;
+}
+
+// w_i rho (1 + cu), one rounding for w_i rho and one for the fused rest.
+__device__ __forceinline__ float ref_of(int i, float rho, float cu) {
+  const float wr = w_of<float>(i) * rho;
+  return fmaf(wr, cu, wr);
+}
+
+// The velocity part U = 3 u of a node's references, as stored (FP16).
+__device__ __forceinline__ __half2 u_ref(float ux, float uy) { return __floats2half2_rn(3.0f * ux, 3.0f * uy); }
+
 // References of the 18 populations pulled at padded index k: the writer of
-// slot i is x - c_i, or x itself when x - c_i is solid (its bounced slot).
-// check: whether fl may hold solid neighbours.
+// slot i is x - c_i (direction i), or x itself when x - c_i is solid (its
+// bounced slot, which holds the value it sent along -c_i). check: whether fl
+// may hold solid neighbours.
 template <typename T, typename C>
-__device__ __forceinline__ void pull_refs(const C* __restrict__ Pref, const Geo& g, int k, uint16_t fl, bool check,
-                                          C ref[2][9]) {
+__device__ __forceinline__ void pull_refs(const C* __restrict__ Pref, const __half2* __restrict__ Uref, const Geo& g,
+                                          int k, uint16_t fl, bool check, C ref[2][9]) {
   if constexpr (kDev<T>) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -56,8 +79,10 @@ __device__ __forceinline__ void pull_refs(const C* __restrict__ Pref, const Geo&
       const int m = self ? k : k - cx_of(i) - cy_of(i) * g.px;
       C a, b;
       ldP(Pref, m, a, b);
-      ref[0][i] = w_of<C>(i) * a;
-      ref[1][i] = w_of<C>(i) * b;
+      const float cd = Uref ? cdot(i, __half22float2(__ldg(Uref + m))) : 0.0f;  // no velocity plane: w_i rho
+      const float cu = (self && i != 0) ? -cd : cd;
+      ref[0][i] = ref_of(i, a, cu);
+      ref[1][i] = ref_of(i, b, cu);
     }
   } else {
 #pragma unroll
@@ -67,20 +92,27 @@ __device__ __forceinline__ void pull_refs(const C* __restrict__ Pref, const Geo&
   }
 }
 
-// References for what a node writes (its own slots and its bounced slots):
-// w_i times its own density rho.
+// References for what a node writes, given its own rho and U (as stored):
+// ref[s][i] for its slot i (direction i). Its bounced slot i holds the value
+// sent along -c_i, whose reference is ref[s][opp(i)].
 template <typename T, typename C>
-__device__ __forceinline__ void write_refs(const C rho[2], C ref[2][9]) {
+__device__ __forceinline__ void write_refs(const C rho[2], float2 U, C ref[2][9]) {
 #pragma unroll
   for (int s = 0; s < 2; ++s)
 #pragma unroll
-    for (int i = 0; i < 9; ++i) ref[s][i] = kDev<T> ? w_of<C>(i) * rho[s] : C(0);
+    for (int i = 0; i < 9; ++i) {
+      if constexpr (kDev<T>)
+        ref[s][i] = ref_of(i, rho[s], cdot(i, U));
+      else
+        ref[s][i] = C(0);
+    }
 }
 
 // ---- K1: densities --------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(128) k_density(const T* __restrict__ f, typename Pop<T>::C* __restrict__ P,
                                                  const typename Pop<T>::C* __restrict__ Pref,
+                                                 const __half2* __restrict__ Uref,
                                                  const uint16_t* __restrict__ flags, Geo g,
                                                  PhysK<typename Pop<T>::C> ph) {
   using C = typename Pop<T>::C;
@@ -90,7 +122,7 @@ __global__ void __launch_bounds__(128) k_density(const T* __restrict__ f, typena
   const uint16_t fl = flags[k];
   if (fl & F_SOLID) return;
   C ref[2][9];
-  pull_refs<T>(Pref, g, k, fl, true, ref);
+  pull_refs<T>(Pref, Uref, g, k, fl, true, ref);
   C fv[2][9];
   gather<T>(f, g, k, ref, fv);
   stP_ghosts(P, g, x, y, density(fv[0]), density(fv[1]));
@@ -114,6 +146,7 @@ __device__ __forceinline__ void coords(const Geo& g, int k, int& x, int& y) {
 template <typename T>
 __device__ __forceinline__ void density_node(const T* __restrict__ f, typename Pop<T>::C* __restrict__ P,
                                              const typename Pop<T>::C* __restrict__ Pref,
+                                             const __half2* __restrict__ Uref,
                                              const uint16_t* __restrict__ flags, const int* __restrict__ list, int t,
                                              const Geo& g) {
   using C = typename Pop<T>::C;
@@ -122,9 +155,9 @@ __device__ __forceinline__ void density_node(const T* __restrict__ f, typename P
   C ref[2][9];
   if constexpr (kDev<T>) {
     const bool edge = e & EDGE_TAG;
-    pull_refs<T>(Pref, g, k, edge ? __ldg(flags + k) : uint16_t(0), edge, ref);
+    pull_refs<T>(Pref, Uref, g, k, edge ? __ldg(flags + k) : uint16_t(0), edge, ref);
   } else {
-    pull_refs<T>(Pref, g, k, 0, false, ref);
+    pull_refs<T>(Pref, Uref, g, k, 0, false, ref);
   }
   C fv[2][9];
   gather<T>(f, g, k, ref, fv);
@@ -142,11 +175,12 @@ __device__ __forceinline__ void density_node(const T* __restrict__ f, typename P
 template <typename T>
 __global__ void __launch_bounds__(256) k_density_list(const T* __restrict__ f, typename Pop<T>::C* __restrict__ P,
                                                       const typename Pop<T>::C* __restrict__ Pref,
+                                                      const __half2* __restrict__ Uref,
                                                       const uint16_t* __restrict__ flags,
                                                       const int* __restrict__ list, int nfluid, Geo g,
                                                       PhysK<typename Pop<T>::C> ph) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < nfluid) density_node<T>(f, P, Pref, flags, list, t, g);
+  if (t < nfluid) density_node<T>(f, P, Pref, Uref, flags, list, t, g);
 }
 
 // The update of collide_node for the FP32 compute type, with the two
@@ -154,12 +188,13 @@ __global__ void __launch_bounds__(256) k_density_list(const T* __restrict__ f, t
 template <typename T>
 __device__ __forceinline__ void collide_node_pair(const T* __restrict__ f, T* __restrict__ fo,
                                                   const float* __restrict__ P, const float* __restrict__ Pref,
+                                                  const __half2* __restrict__ Uref, __half2* __restrict__ Uo,
                                                   const uint16_t* __restrict__ flags, unsigned e, bool warp_edge,
                                                   bool warp_border, const Geo& g, const PhysK<float>& ph) {
   const int k = (int)(e & ~LIST_TAGS);
   const uint16_t fl = warp_edge ? __ldg(flags + k) : uint16_t(0);
   float ref[2][9];
-  pull_refs<T>(Pref, g, k, fl, warp_edge, ref);
+  pull_refs<T>(Pref, Uref, g, k, fl, warp_edge, ref);
   float2 fp[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
@@ -172,9 +207,23 @@ __device__ __forceinline__ void collide_node_pair(const T* __restrict__ f, T* __
     const int m = k + cx_of(i) + cy_of(i) * g.px;
     q[i] = __ldg(reinterpret_cast<const float2*>(P) + m);
   }
-  const float2 rho = warp_edge ? update_pair<true>(fp, q, fl, ph) : update_pair<false>(fp, q, fl, ph);
+  float ux, uy;
+  const float2 rho = warp_edge ? update_pair<true>(fp, q, fl, ph, ux, uy) : update_pair<false>(fp, q, fl, ph, ux, uy);
   const float rr[2] = {rho.x, rho.y};
-  write_refs<T>(rr, ref);
+  float2 U = make_float2(0.0f, 0.0f);
+  if constexpr (kDev<T>) {
+    if (Uo) {
+    const __half2 uh = u_ref(ux, uy);
+    U = __half22float2(uh);
+    Uo[k] = uh;
+    if (warp_border) {
+      int x, y;
+      coords(g, k, x, y);
+      for_ghost_images(g, x, y, [&](int kk) { Uo[kk] = uh; });
+    }
+    }
+  }
+  write_refs<T>(rr, U, ref);
   if (!warp_border) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -185,7 +234,7 @@ __device__ __forceinline__ void collide_node_pair(const T* __restrict__ f, T* __
       for (int i = 1; i < 9; ++i) {
         if (!(fl & nb_bit(opp_of(i)))) continue;
         const int ks = k - cx_of(i) - cy_of(i) * g.px;
-        Pop<T>::st2(fo, pslot(g, i, ks), fp[opp_of(i)].x, fp[opp_of(i)].y, ref[0][i], ref[1][i]);
+        Pop<T>::st2(fo, pslot(g, i, ks), fp[opp_of(i)].x, fp[opp_of(i)].y, ref[0][opp_of(i)], ref[1][opp_of(i)]);
       }
     }
   } else {
@@ -218,6 +267,7 @@ template <typename T>
 __device__ __forceinline__ void collide_node(const T* __restrict__ f, T* __restrict__ fo,
                                              const typename Pop<T>::C* __restrict__ P,
                                              const typename Pop<T>::C* __restrict__ Pref,
+                                             const __half2* __restrict__ Uref, __half2* __restrict__ Uo,
                                              const uint16_t* __restrict__ flags, const int* __restrict__ list,
                                              int t, int nfluid, const Geo& g,
                                              const PhysK<typename Pop<T>::C>& ph) {
@@ -228,13 +278,13 @@ __device__ __forceinline__ void collide_node(const T* __restrict__ f, T* __restr
   const bool warp_border = __any_sync(0xffffffffu, (e & BORDER_TAG) != 0u);
   if (!valid) return;
   if constexpr (sizeof(C) == 4) {
-    collide_node_pair<T>(f, fo, P, Pref, flags, e, warp_edge, warp_border, g, ph);
+    collide_node_pair<T>(f, fo, P, Pref, Uref, Uo, flags, e, warp_edge, warp_border, g, ph);
     return;
-  }
+  } else {
   const int k = (int)(e & ~LIST_TAGS);
   const uint16_t fl = warp_edge ? __ldg(flags + k) : uint16_t(0);
   C ref[2][9];
-  pull_refs<T>(Pref, g, k, fl, warp_edge, ref);
+  pull_refs<T>(Pref, Uref, g, k, fl, warp_edge, ref);
   C fv[2][9];
   gather<T>(f, g, k, ref, fv);
   const C rho[2] = {density(fv[0]), density(fv[1])};
@@ -253,7 +303,7 @@ __device__ __forceinline__ void collide_node(const T* __restrict__ f, T* __restr
   const C ux = ((jxA + jxB) + C(0.5) * (F[0][0] + F[1][0])) * inv;
   const C uy = ((jyA + jyB) + C(0.5) * (F[0][1] + F[1][1])) * inv;
   collide(fv, rho, ux, uy, F, ph.omega, ph.kF);
-  write_refs<T>(rho, ref);
+  write_refs<T>(rho, make_float2(0.0f, 0.0f), ref);  // the FP64 compute type stores 8-byte populations
   if (!warp_border) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) Pop<T>::st2(fo, pslot(g, i, k), fv[0][i], fv[1][i], ref[0][i], ref[1][i]);
@@ -264,17 +314,20 @@ __device__ __forceinline__ void collide_node(const T* __restrict__ f, T* __restr
     store_node(fo, g, x, y, k, fv, ref);
     store_bounced(fo, g, x, y, fl, fv, ref);
   }
+  }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(COLLIDE_THREADS, 8) k_collide_list(const T* __restrict__ f, T* __restrict__ fo,
                                                          const typename Pop<T>::C* __restrict__ P,
                                                          const typename Pop<T>::C* __restrict__ Pref,
+                                                         const __half2* __restrict__ Uref,
+                                                         __half2* __restrict__ Uo,
                                                          const uint16_t* __restrict__ flags,
                                                          const int* __restrict__ list, int nfluid, Geo g,
                                                          PhysK<typename Pop<T>::C> ph) {
   prefetch_list_ahead<COLLIDE_THREADS>(list, nfluid);
-  collide_node<T>(f, fo, P, Pref, flags, list, blockIdx.x * blockDim.x + threadIdx.x, nfluid, g, ph);
+  collide_node<T>(f, fo, P, Pref, Uref, Uo, flags, list, blockIdx.x * blockDim.x + threadIdx.x, nfluid, g, ph);
 }
 
 // ---- K2: virtual solid density of Eq. 8 over the interface-solid list -----
@@ -365,15 +418,17 @@ __global__ void __launch_bounds__(128) k_virtual_density(C* __restrict__ P, cons
 }
 
 
-// ---- K3: fused force + collide + stream (pull) ---------------------------
-// MODE 0: write post-collision populations. MODE 1: write moments (rho, u)
-// instead. MODE 2: write forces.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(128) k_collide(const T* __restrict__ f, T* __restrict__ fo,
-                                                 const typename Pop<T>::C* __restrict__ P,
+// ---- Evaluation of the current state: moments or forces -----------------
+// MODE 1: write the moments (rho^A, rho^B, u of Eq. 3). MODE 2: write the
+// forces (Eq. 5 + Eq. 7). The populations are not changed. O: the type of
+// the output arrays (double, or float for the FP32 host interface).
+template <typename T, int MODE, typename O = double>
+__global__ void __launch_bounds__(128) k_collide(const T* __restrict__ f, const typename Pop<T>::C* __restrict__ P,
                                                  const typename Pop<T>::C* __restrict__ Pref,
+                                                 const __half2* __restrict__ Uref,
                                                  const uint16_t* __restrict__ flags, Geo g,
-                                                 PhysK<typename Pop<T>::C> ph, double* __restrict__ out) {
+                                                 PhysK<typename Pop<T>::C> ph, O* __restrict__ out) {
+  static_assert(MODE == 1 || MODE == 2, "evaluation modes only");
   using C = typename Pop<T>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= g.nx) return;
@@ -382,15 +437,11 @@ __global__ void __launch_bounds__(128) k_collide(const T* __restrict__ f, T* __r
   const int64_t n = (int64_t)y * g.nx + x;
   const int64_t N = (int64_t)g.nx * g.ny;
   if (fl & F_SOLID) {
-    if (MODE == 1) {
-      out[n] = 0; out[N + n] = 0; out[2 * N + n] = 0; out[3 * N + n] = 0;
-    } else if (MODE == 2) {
-      out[n] = 0; out[N + n] = 0; out[2 * N + n] = 0; out[3 * N + n] = 0;
-    }
+    out[n] = 0; out[N + n] = 0; out[2 * N + n] = 0; out[3 * N + n] = 0;
     return;
   }
   C ref[2][9];
-  pull_refs<T>(Pref, g, k, fl, true, ref);
+  pull_refs<T>(Pref, Uref, g, k, fl, true, ref);
   C fv[2][9];
   gather<T>(f, g, k, ref, fv);
   C rho[2] = {density(fv[0]), density(fv[1])};
@@ -405,30 +456,28 @@ __global__ void __launch_bounds__(128) k_collide(const T* __restrict__ f, T* __r
   const C ux = ((jxA + jxB) + C(0.5) * (F[0][0] + F[1][0])) * inv;
   const C uy = ((jyA + jyB) + C(0.5) * (F[0][1] + F[1][1])) * inv;
   if (MODE == 1) {
-    out[n] = rho[0];
-    out[N + n] = rho[1];
-    out[2 * N + n] = ux;
-    out[3 * N + n] = uy;
-    return;
+    out[n] = O(rho[0]);
+    out[N + n] = O(rho[1]);
+    out[2 * N + n] = O(ux);
+    out[3 * N + n] = O(uy);
+  } else {
+    out[n] = O(F[0][0]);
+    out[N + n] = O(F[0][1]);
+    out[2 * N + n] = O(F[1][0]);
+    out[3 * N + n] = O(F[1][1]);
   }
-  if (MODE == 2) {
-    out[n] = F[0][0];
-    out[N + n] = F[0][1];
-    out[2 * N + n] = F[1][0];
-    out[3 * N + n] = F[1][1];
-    return;
-  }
-  const C omega[2] = {C(ph.omega[0]), C(ph.omega[1])};
-  const C kF[2] = {C(ph.kF[0]), C(ph.kF[1])};
-  collide(fv, rho, ux, uy, F, omega, kF);
-  write_refs<T>(rho, ref);
-  store_node(fo, g, x, y, k, fv, ref);
-  store_bounced(fo, g, x, y, fl, fv, ref);
+}
+
+// Widen n floats to doubles (separate arrays).
+static __global__ void k_widen(const float* __restrict__ in, double* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)in[i];
 }
 
 // ---- post-streaming populations out / in ---------------------------------
 template <typename T>
 __global__ void k_get_populations(const T* __restrict__ f, const typename Pop<T>::C* __restrict__ Pref,
+                                  const __half2* __restrict__ Uref,
                                   const uint16_t* __restrict__ flags, Geo g,
                                   PhysK<typename Pop<T>::C> ph, double* __restrict__ out) {
   using C = typename Pop<T>::C;
@@ -443,7 +492,7 @@ __global__ void k_get_populations(const T* __restrict__ f, const typename Pop<T>
       for (int i = 0; i < 9; ++i) fv[s][i] = 0;
   } else {
     C ref[2][9];
-    pull_refs<T>(Pref, g, k, fl, true, ref);
+    pull_refs<T>(Pref, Uref, g, k, fl, true, ref);
     gather<T>(f, g, k, ref, fv);
   }
   for (int s = 0; s < 2; ++s)
@@ -464,10 +513,11 @@ __device__ __forceinline__ int64_t wrap_compact(const Geo& g, int x, int y) {
 // is solid; and slot i of a solid node x - c_i holds O_i(x) (the bounced
 // value x receives). SRC 0: O is read from fin [2][9][ny][nx]. SRC 1: O is
 // the equilibrium of Eq. 2 of the rho/u arrays.
-// The node's own post-streaming density is written to Pref as the encoding
-// reference of everything the node stores here.
+// The node's own post-streaming density (to Pref) and 3 u (to Uo, 16-bit
+// storage only; u = the momentum of the received populations over their
+// density) are the encoding references of everything the node stores here.
 template <typename T, int SRC>
-__global__ void k_set_state(T* __restrict__ f, typename Pop<T>::C* __restrict__ Pref,
+__global__ void k_set_state(T* __restrict__ f, typename Pop<T>::C* __restrict__ Pref, __half2* __restrict__ Uo,
                             const uint16_t* __restrict__ flags, Geo g, PhysK<typename Pop<T>::C> ph,
                             const double* __restrict__ fin, const double* __restrict__ rA,
                             const double* __restrict__ rB, const double* __restrict__ ux,
@@ -513,8 +563,22 @@ __global__ void k_set_state(T* __restrict__ f, typename Pop<T>::C* __restrict__ 
     rho0[s] = r;
   }
   stP_ghosts(Pref, g, x, y, rho0[0], rho0[1]);
+  float2 U = make_float2(0.0f, 0.0f);
+  if (kDev<T> && Uo) {
+    C jx = C(0), jy = C(0);
+    for (int s = 0; s < 2; ++s)
+      for (int j = 1; j < 9; ++j) {
+        const C o = O(n, own, s, j);
+        jx += C(cx_of(j)) * o;
+        jy += C(cy_of(j)) * o;
+      }
+    const C r = rho0[0] + rho0[1];
+    const __half2 uh = u_ref(r > C(0) ? jx / r : C(0), r > C(0) ? jy / r : C(0));
+    U = __half22float2(uh);
+    put_with_ghosts(Uo, g, x, y, uh);
+  }
   C ref[2][9];
-  write_refs<T>(rho0, ref);
+  write_refs<T>(rho0, U, ref);
   C fv[2][9];
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
@@ -542,6 +606,7 @@ __global__ void k_set_state(T* __restrict__ f, typename Pop<T>::C* __restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(256) k_mass_partial(const T* __restrict__ f,
                                                       const typename Pop<T>::C* __restrict__ Pref,
+                                                      const __half2* __restrict__ Uref,
                                                       const uint16_t* __restrict__ flags, Geo g,
                                                       PhysK<typename Pop<T>::C> ph, double* __restrict__ partial) {
   using C = typename Pop<T>::C;
@@ -554,11 +619,13 @@ __global__ void __launch_bounds__(256) k_mass_partial(const T* __restrict__ f,
     if (flags[k] & F_SOLID) continue;
     // a node's own slots were written by the node itself
     C rw[2] = {C(0), C(0)};
+    float2 U = make_float2(0.0f, 0.0f);
     if (kDev<T>) {
       ldP(Pref, k, rw[0], rw[1]);
+      if (Uref) U = __half22float2(Uref[k]);
     }
     C ref[2][9];
-    write_refs<T>(rw, ref);
+    write_refs<T>(rw, U, ref);
     double r[2] = {0.0, 0.0};
     for (int i = 0; i < 9; ++i) {
       C a, b;

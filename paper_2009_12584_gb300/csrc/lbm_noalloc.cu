@@ -2,6 +2,8 @@
 // that cannot allocate device memory. Its scratch (one partial sum per block
 // and component) lives in a file-scope __device__ array instead of a
 // caller-provided workspace; see include/lbm.h for the contract.
+#include <cuda.h>  // CUcontext; the two driver calls are resolved through the runtime, not linked
+
 #include <mutex>
 
 #include "lbm.h"
@@ -13,14 +15,27 @@ constexpr int NA_PER_THREAD = 16;
 constexpr int64_t NA_BLOCK_NODES = (int64_t)NA_THREADS * NA_PER_THREAD;  // 4096 nodes per block
 constexpr int NA_MAX_BLOCKS = 16384;                                     // 2 x 16384 doubles = 256 KiB
 constexpr int64_t NA_MAX_NODES = NA_BLOCK_NODES * NA_MAX_BLOCKS;         // 67,108,864 = 8192^2
-constexpr int NA_MAX_DEVICES = 64;
+constexpr int NA_MAX_CONTEXTS = 64;
 
 // Shared by every call on a device and kept until the process exits.
 static __device__ __align__(256) double g_mass_partials[2 * NA_MAX_BLOCKS];
 
-// Device address of g_mass_partials per device, looked up once.
+// Device address of g_mass_partials per CUDA context, looked up once in
+// each. Contexts are told apart by the driver's context identifier, which
+// is unique for the life of the process: a context destroyed (for instance
+// by cudaDeviceReset) and created again gets a new identifier and a new
+// lookup, so no stale address is ever used.
+struct AddrEntry {
+  unsigned long long ctx_id;
+  double* addr;
+};
 std::mutex g_lock;
-double* g_addr[NA_MAX_DEVICES] = {};
+AddrEntry g_addr[NA_MAX_CONTEXTS] = {};
+int g_next = 0;
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
 
 // Block b sums the fluid nodes of [b * 4096, (b + 1) * 4096) in a fixed
 // order: each thread its 16 nodes (stride 256), then a shuffle tree per
@@ -68,19 +83,49 @@ __global__ void k_field_mass_final(const double* __restrict__ partial, int nbloc
   if (lane == 0) out[s] = v;
 }
 
-// Set-up, once per device with that device current: the host-side name of a
-// __device__ array is not a device address, so ask the runtime for it.
-lbm_status partials_address(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ERR_CUDA;
-  if (dev < 0 || dev >= NA_MAX_DEVICES) return LBM_ERR_ARG;
-  std::lock_guard<std::mutex> guard(g_lock);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_mass_partials) != cudaSuccess || p == nullptr) return LBM_ERR_CUDA;
-    g_addr[dev] = (double*)p;
+// Identifier of the calling thread's current context (0 if none is current
+// yet). Call with g_lock held.
+lbm_status current_context_id(unsigned long long* id) {
+  if (!g_ctx_current || !g_ctx_id) {
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&g_ctx_current, 12000, cudaEnableDefault,
+                                         &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&g_ctx_id, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+      g_ctx_current = nullptr;
+      g_ctx_id = nullptr;
+      return LBM_ERR_CUDA;
+    }
   }
-  *out = g_addr[dev];
+  CUcontext ctx = nullptr;
+  if (g_ctx_current(&ctx) != CUDA_SUCCESS) return LBM_ERR_CUDA;
+  *id = 0;
+  if (ctx && g_ctx_id(ctx, id) != CUDA_SUCCESS) return LBM_ERR_CUDA;
+  return LBM_OK;
+}
+
+// Set-up, once per context (so once per device for the runtime's primary
+// contexts), with that context current: the host-side name of a __device__
+// array is not a device address, so ask the runtime for it.
+lbm_status partials_address(double** out) {
+  std::lock_guard<std::mutex> guard(g_lock);
+  unsigned long long id = 0;
+  lbm_status s = current_context_id(&id);
+  if (s) return s;
+  if (id != 0)
+    for (const AddrEntry& e : g_addr)
+      if (e.ctx_id == id && e.addr) {
+        *out = e.addr;
+        return LBM_OK;
+      }
+  // the lookup makes the device's primary context current if none was
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_mass_partials) != cudaSuccess || p == nullptr) return LBM_ERR_CUDA;
+  if (id == 0 && ((s = current_context_id(&id)) || id == 0)) return s ? s : LBM_ERR_CUDA;
+  g_addr[g_next] = AddrEntry{id, (double*)p};
+  g_next = (g_next + 1) % NA_MAX_CONTEXTS;
+  *out = (double*)p;
   return LBM_OK;
 }
 
@@ -96,6 +141,8 @@ extern "C" lbm_status lbm_field_mass_noalloc(const double* d_rhoA, const double*
   if (s) return s;
   const int nblocks = (int)((n + NA_BLOCK_NODES - 1) / NA_BLOCK_NODES);
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  // an error left by earlier work is the caller's: report it without clearing it
+  if (cudaPeekAtLastError() != cudaSuccess) return LBM_ERR_CUDA;
   k_field_mass_partial<<<nblocks, NA_THREADS, 0, st>>>(d_rhoA, d_rhoB, d_mask, n, partial);
   if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
   k_field_mass_final<<<1, 64, 0, st>>>(partial, nblocks, d_out);

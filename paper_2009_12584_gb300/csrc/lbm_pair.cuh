@@ -30,12 +30,14 @@ __device__ __forceinline__ void weighted_sum2(const float2 q[9], float2& sx, flo
 }
 
 // Eq. 5 (fluid neighbours) plus Eq. 7 for both components. q[i]: the
-// density plane (rho, or rho~ at interface-solid nodes) at x + c_i.
+// density plane (rho, or rho~ at interface-solid nodes) at x + c_i. With
+// ph.uniform (the improved scheme with G_As = G_Bs = G_AB and Eq. 7's cross
+// pairing) both sums are one weighted sum over the plane, the bulk formula.
 template <bool GENERAL>
 __device__ __forceinline__ void interaction_force2(const PhysK<float>& ph, uint16_t fl, float2 rho,
                                                    const float2 q[9], float2& Fx, float2& Fy) {
   const float2 G = f2(ph.G_AB);
-  if (!GENERAL) {
+  if (!GENERAL || ph.uniform) {
     float2 ax, ay;
     weighted_sum2(q, ax, ay);
     // component s feels the other component's density
@@ -135,10 +137,11 @@ __device__ __forceinline__ void collide2(float2 f[9], float2 rho, float ux, floa
 // the pulled populations f_i of both components on entry and f*_i on exit;
 // q[i] the density plane at x + c_i. GENERAL: the node may have solid
 // neighbours (fl holds the neighbour bits); a node without any gets the
-// same result on either path. Returns rho of both components.
+// same result on either path. Returns rho of both components and, in
+// ux_out, uy_out, the velocity u of Eq. 3 the collision used.
 template <bool GENERAL>
 __device__ __forceinline__ float2 update_pair(float2 fp[9], const float2 q[9], uint16_t fl,
-                                              const PhysK<float>& ph) {
+                                              const PhysK<float>& ph, float& ux_out, float& uy_out) {
   const float2 rho = add2(add2(add2(fp[0], add2(fp[1], fp[3])), add2(fp[2], fp[4])),
                           add2(add2(fp[5], fp[7]), add2(fp[6], fp[8])));
   float2 Fx, Fy;
@@ -151,6 +154,8 @@ __device__ __forceinline__ float2 update_pair(float2 fp[9], const float2 q[9], u
   const float ux = ((jx.x + jx.y) + 0.5f * (Fx.x + Fx.y)) * inv;
   const float uy = ((jy.x + jy.y) + 0.5f * (Fy.x + Fy.y)) * inv;
   collide2(fp, rho, ux, uy, Fx, Fy, ph);
+  ux_out = ux;
+  uy_out = uy;
   return rho;
 }
 

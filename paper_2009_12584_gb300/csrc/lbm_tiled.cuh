@@ -115,24 +115,28 @@ static __global__ void __launch_bounds__(TILE_LIST_THREADS) k_tile_lists(const u
 }
 
 // One CTA per tile; dynamic shared memory holds f*(t+1) of the region as
-// nine planes of component pairs, [9][TILE_RS]. 16-bit storage: Pref holds
-// the densities the pulled populations were encoded with (their writers'
-// rho(t - 1)), the node encodes what it stores with its own rho(t), and
-// shared memory keeps each value as the next step will decode it (encoded
-// and decoded again), so that phase 2 sums exactly what the next step
-// pulls, like the density pass. Pref is not read for 4- and 8-byte storage.
+// nine planes of component pairs, [9][TILE_RS]. 16-bit storage: Pref and
+// Uref hold the densities and velocities the pulled populations were
+// encoded with (their writers' rho(t - 1), 3 u(t - 1)), the node encodes
+// what it stores with its own rho(t) and 3 u(t) (written to Uo), and shared
+// memory keeps each value as the next step will decode it (encoded and
+// decoded again), so that phase 2 sums exactly what the next step pulls,
+// like the density pass. Pref, Uref and Uo are not used for 4- and 8-byte
+// storage.
+// The work of one CTA on tile `tile` of n_tiles (one simulation).
 template <typename T>
-__global__ void __launch_bounds__(TILE_THREADS, TILE_MINB)
-    k_tile(const T* __restrict__ f, T* __restrict__ fo, const typename Pop<T>::C* __restrict__ P,
-           const typename Pop<T>::C* __restrict__ Pref, typename Pop<T>::C* __restrict__ Po,
-           const uint16_t* __restrict__ flags,
-           const uint16_t* __restrict__ entries, const int* __restrict__ offsets, const int* __restrict__ nown,
-           Geo g, int ntx, PhysK<typename Pop<T>::C> ph) {
+__device__ __forceinline__ void tile_step(int tile, int n_tiles, const T* __restrict__ f, T* __restrict__ fo,
+                                          const typename Pop<T>::C* __restrict__ P,
+                                          const typename Pop<T>::C* __restrict__ Pref,
+                                          const __half2* __restrict__ Uref, __half2* __restrict__ Uo,
+                                          typename Pop<T>::C* __restrict__ Po, const uint16_t* __restrict__ flags,
+                                          const uint16_t* __restrict__ entries, const int* __restrict__ offsets,
+                                          const int* __restrict__ nown, const Geo& g, int ntx,
+                                          const PhysK<typename Pop<T>::C>& ph) {
   using C = typename Pop<T>::C;
   using V = typename CPair<C>::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* s = reinterpret_cast<V*>(smem_raw);
-  const int tile = blockIdx.x;
   const int n_own = nown[tile];
   if (n_own == 0) return;  // the whole CTA: nothing owned, nothing to store
   const int e0 = offsets[tile], n_all = offsets[tile + 1] - e0;
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MINB)
   // 128-byte line per 64 entries, enough lines for a full region).
   constexpr int ENTRY_LINES = (TILE_RS + 63) / 64;
   static_assert(ENTRY_LINES <= TILE_THREADS, "one thread per line");
-  if (threadIdx.x < ENTRY_LINES && tile + TILE_AHEAD < (int)gridDim.x) {
+  if (threadIdx.x < ENTRY_LINES && tile + TILE_AHEAD < n_tiles) {
     const int e1 = __ldg(offsets + tile + TILE_AHEAD);
     asm volatile("prefetch.global.L2 [%0];" ::"l"(entries + e1 + threadIdx.x * 64));
   }
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MINB)
     const int k = korg + row * g.px + col;
     const uint16_t fl = warp_edge ? __ldg(flags + k) : uint16_t(0);
     C ref[2][9];  // storage references (zero for 4- and 8-byte populations)
-    pull_refs<T>(Pref, g, k, fl, warp_edge, ref);
+    pull_refs<T>(Pref, Uref, g, k, fl, warp_edge, ref);
     C fv[2][9];
 #pragma unroll
     for (int i = 0; i < 9; ++i)
@@ -176,9 +180,19 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MINB)
       for (int i = 0; i < 9; ++i)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(f + pslot(g, i, k2 - cx_of(i) - cy_of(i) * g.px)));
     }
-    C rho[2];
-    march_update<C>(fv, nbP, fl, warp_edge, ph, rho);
-    write_refs<T>(rho, ref);
+    C rho[2], u[2];
+    march_update<C>(fv, nbP, fl, warp_edge, ph, rho, u);
+    float2 U = make_float2(0.0f, 0.0f);
+    if (kDev<T> && Uo) {
+      const __half2 uh = u_ref(u[0], u[1]);
+      U = __half22float2(uh);
+      if (t < n_own) {
+        Uo[k] = uh;
+        if (e & TE_BORDER)
+          for_ghost_images(g, x0 - 1 + col, y0 - 1 + row, [&](int kk) { Uo[kk] = uh; });
+      }
+    }
+    write_refs<T>(rho, U, ref);
     if (t < n_own) {
       if (!warp_border) {
 #pragma unroll
@@ -223,6 +237,17 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MINB)
 }
 
 template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS, TILE_MINB)
+    k_tile(const T* __restrict__ f, T* __restrict__ fo, const typename Pop<T>::C* __restrict__ P,
+           const typename Pop<T>::C* __restrict__ Pref, const __half2* __restrict__ Uref,
+           __half2* __restrict__ Uo, typename Pop<T>::C* __restrict__ Po,
+           const uint16_t* __restrict__ flags,
+           const uint16_t* __restrict__ entries, const int* __restrict__ offsets, const int* __restrict__ nown,
+           Geo g, int ntx, PhysK<typename Pop<T>::C> ph) {
+  tile_step<T>(blockIdx.x, gridDim.x, f, fo, P, Pref, Uref, Uo, Po, flags, entries, offsets, nown, g, ntx, ph);
+}
+
+template <typename T>
 constexpr size_t tile_smem() {
   return (size_t)9 * TILE_RS * sizeof(typename CPair<typename Pop<T>::C>::V);
 }
@@ -231,7 +256,8 @@ constexpr size_t tile_smem() {
 // the kernel's dynamic shared memory limit has been raised.
 template <typename T>
 inline lbm_status launch_tiled(const Geo& g, const Phys& ph, const T* fin, T* fout, const typename Pop<T>::C* P,
-                               const typename Pop<T>::C* Pref, typename Pop<T>::C* Po, const uint16_t* flags,
+                               const typename Pop<T>::C* Pref, const __half2* Uref, __half2* Uo,
+                               typename Pop<T>::C* Po, const uint16_t* flags,
                                const uint16_t* entries, const int* offsets, const int* nown, bool* smem_set,
                                cudaStream_t stream) {
   constexpr size_t SMEM = tile_smem<T>();
@@ -243,7 +269,7 @@ inline lbm_status launch_tiled(const Geo& g, const Phys& ph, const T* fin, T* fo
   }
   const int ntx = (g.nx + TILE_W - 1) / TILE_W;
   const int64_t nt = tile_count(g);
-  kern<<<(unsigned)nt, TILE_THREADS, SMEM, stream>>>(fin, fout, P, Pref, Po, flags, entries, offsets, nown, g, ntx,
+  kern<<<(unsigned)nt, TILE_THREADS, SMEM, stream>>>(fin, fout, P, Pref, Uref, Uo, Po, flags, entries, offsets, nown, g, ntx,
                                                      kphys<typename Pop<T>::C>(ph));
   return LBM_OK;
 }

@@ -1,0 +1,245 @@
+// Tiled single-pass step with the tile's inputs staged by the Tensor Memory
+// Accelerator (TMA): FP32 storage, the same per-tile lists, node arithmetic
+// and results (bit for bit) as k_tile.
+//
+// k_tile pulls every population of every listed node with its own load
+// and waits for them (list entry -> pulls -> update is a chain of dependent
+// global round trips per node). Here a persistent CTA (one per SM) walks its
+// tiles (blockIdx.x, + gridDim.x, ...) and, while it updates one tile, one
+// thread has the TMA copy the next tile's inputs into the other half of a
+// double buffer: the nine population planes and the density plane over the
+// (TILE_W + 4) x (TILE_H + 4) window that the tile and its one-node ring
+// pull from (ten 2-D boxes, no per-node address arithmetic, no registers
+// held by loads in flight). An mbarrier per buffer counts the bytes in; the
+// wait on it is bounded (see TMA_SPIN_LIMIT). Stores, the ring, phase 2
+// and the periodic images are those of k_tile.
+#pragma once
+
+#include <cuda.h>  // CUtensorMap
+
+#include "lbm_tiled.cuh"
+
+namespace lbm {
+
+constexpr int TMA_WW = TILE_W + 4;                  // window columns (pairs): x0 - 2 ... x0 + TILE_W + 1
+constexpr int TMA_WH = TILE_H + 4;                  // window rows
+constexpr int TMA_BOX_X = 2 * TMA_WW;               // floats per window row (component pairs)
+constexpr int TMA_PLANE_BYTES = TMA_BOX_X * TMA_WH * 4;
+constexpr int TMA_SLOT_BYTES = (TMA_PLANE_BYTES + 127) / 128 * 128;  // 128-byte aligned destinations
+constexpr int TMA_BUF_BYTES = 10 * TMA_SLOT_BYTES;  // nine population planes and the density plane
+#ifndef LBM_TMA_THREADS
+#define LBM_TMA_THREADS 512
+#endif
+constexpr int TMA_THREADS = LBM_TMA_THREADS;
+// try_wait rounds before a CTA gives up on a copy and reports it (each round
+// is a hardware-bounded suspend of the waiting thread)
+constexpr unsigned TMA_SPIN_LIMIT = 1u << 24;
+static_assert(TMA_BOX_X <= 256 && TMA_WH <= 256, "TMA box dimensions are at most 256");
+static_assert((TMA_BOX_X * 4) % 16 == 0, "the box's inner extent must be a multiple of 16 bytes");
+static_assert(TILE_W % 2 == 0, "window x starts must be 16-byte aligned: 4 * 2 * (x0 - 2 + LP) % 16 == 0");
+
+template <typename T>
+constexpr size_t tma_smem() {
+  return 2 * (size_t)TMA_BUF_BYTES + (size_t)9 * TILE_RS * sizeof(float2) + 128;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Wait for the phase with the given parity to complete; false after
+// TMA_SPIN_LIMIT rounds.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (unsigned r = 0; r < TMA_SPIN_LIMIT; ++r) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// One TMA box of a rank-3 tensor (x, y, plane) into shared memory, counted
+// on bar.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// The next tile this CTA owns after tile `from` (stride gridDim.x) that has
+// nodes of its own, or -1.
+__device__ __forceinline__ int next_tile(const int* __restrict__ nown, int from, int n_tiles) {
+  for (int t = from; t < n_tiles; t += gridDim.x)
+    if (__ldg(nown + t) > 0) return t;
+  return -1;
+}
+
+// Issue the ten copies of tile `tile`'s window into buffer `buf` (one thread).
+__device__ __forceinline__ void tma_issue(unsigned char* buf, uint64_t* bar, const CUtensorMap* mapf,
+                                          const CUtensorMap* mapP, int tile, int ntx) {
+  const int x0 = (tile % ntx) * TILE_W, y0 = (tile / ntx) * TILE_H;
+  // padded coordinates of the window's first pair: column x0 - 2 + LP (its
+  // first float, times 4 bytes, is 16-byte aligned: TILE_W is even), row
+  // y0 - 2 + GH
+  const int xf = 2 * (x0 - 2 + LP), yw = y0 - 2 + GH;
+  // order the generic-proxy reads of this buffer (the previous tile) before
+  // the copies' writes
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect_tx(bar, 10u * TMA_PLANE_BYTES);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) tma_load_3d(buf + i * TMA_SLOT_BYTES, mapf, xf, yw, i, bar);
+  tma_load_2d(buf + 9 * TMA_SLOT_BYTES, mapP, xf, yw, bar);
+}
+
+// err: set to 1 when a copy was not seen to complete within the bound (the
+// CTA then stops). The host reads it at its next synchronising call.
+static __global__ void __launch_bounds__(TMA_THREADS, 1)
+    k_tile_tma(const __grid_constant__ CUtensorMap mapf, const __grid_constant__ CUtensorMap mapP,
+               float* __restrict__ fo, float* __restrict__ Po, const uint16_t* __restrict__ flags,
+               const uint16_t* __restrict__ entries, const int* __restrict__ offsets, const int* __restrict__ nown,
+               Geo g, int ntx, int n_tiles, PhysK<float> ph, int* __restrict__ err) {
+  using V = float2;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  unsigned char* buf[2] = {base, base + TMA_BUF_BYTES};
+  V* s = reinterpret_cast<V*>(base + 2 * TMA_BUF_BYTES);  // f*(t+1) of the region, [9][TILE_RS]
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int tile_of[2];
+  const float zr[2][9] = {};  // storage references: zero for 4-byte populations
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const int t0 = next_tile(nown, blockIdx.x, n_tiles);
+    tile_of[0] = t0;
+    if (t0 >= 0) tma_issue(buf[0], &bar[0], &mapf, &mapP, t0, ntx);
+  }
+  __syncthreads();
+  uint32_t parity[2] = {0, 0};
+  for (int n = 0;; ++n) {
+    const int cur = n & 1;
+    const int tile = tile_of[cur];
+    if (tile < 0) break;
+    if (threadIdx.x == 0) {
+      // the next tile's window into the other buffer, freed by the barrier
+      // that ended the previous iteration; its list entries towards L2
+      const int t1 = next_tile(nown, tile + gridDim.x, n_tiles);
+      tile_of[cur ^ 1] = t1;
+      if (t1 >= 0) {
+        tma_issue(buf[cur ^ 1], &bar[cur ^ 1], &mapf, &mapP, t1, ntx);
+        const int e1 = __ldg(offsets + t1), n1 = __ldg(offsets + t1 + 1) - e1;
+        for (int l = 0; l < n1; l += 64) asm volatile("prefetch.global.L2 [%0];" ::"l"(entries + e1 + l));
+      }
+    }
+    const bool ok = mbar_wait(&bar[cur], parity[cur]);
+    if (__syncthreads_or(!ok)) {
+      // a copy did not complete within the bound: report it and stop this
+      // CTA after waiting (bounded) for the copies it has in flight
+      if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        mbar_wait(&bar[cur], parity[cur]);
+        if (tile_of[cur ^ 1] >= 0) mbar_wait(&bar[cur ^ 1], parity[cur ^ 1]);
+      }
+      break;
+    }
+    parity[cur] ^= 1;
+    const float* win = reinterpret_cast<const float*>(buf[cur]);
+    const int n_own = nown[tile];
+    const int e0 = offsets[tile], n_all = offsets[tile + 1] - e0;
+    const int x0 = (tile % ntx) * TILE_W, y0 = (tile / ntx) * TILE_H;
+    const int korg = g.idx(x0 - 1, y0 - 1);  // padded index of region slot 0
+    for (int b = 0; b < n_all; b += TMA_THREADS) {
+      const int t = b + threadIdx.x;
+      const bool valid = t < n_all;
+      const uint16_t e = valid ? __ldg(entries + e0 + t) : uint16_t(0);
+      const bool warp_edge = __any_sync(0xffffffffu, (e & TE_SOLIDNB) != 0);
+      const bool warp_border = __any_sync(0xffffffffu, (e & TE_BORDER) != 0);
+      if (!valid) continue;
+      const int slot = e & TE_SLOT;
+      const int row = slot / TILE_RW, col = slot - row * TILE_RW;
+      const int k = korg + row * g.px + col;
+      const uint16_t fl = warp_edge ? __ldg(flags + k) : uint16_t(0);
+      // region slot (row, col) is window pair (row + 1, col + 1)
+      const int wc = (row + 1) * TMA_BOX_X + 2 * (col + 1);
+      float fv[2][9], nbP[2][9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const V v = *reinterpret_cast<const V*>(win + i * (TMA_SLOT_BYTES / 4) + wc - cy_of(i) * TMA_BOX_X -
+                                                2 * cx_of(i));
+        fv[0][i] = v.x;
+        fv[1][i] = v.y;
+      }
+      nbP[0][0] = nbP[1][0] = 0.0f;
+#pragma unroll
+      for (int i = 1; i < 9; ++i) {
+        const V v = *reinterpret_cast<const V*>(win + 9 * (TMA_SLOT_BYTES / 4) + wc + cy_of(i) * TMA_BOX_X +
+                                                2 * cx_of(i));
+        nbP[0][i] = v.x;
+        nbP[1][i] = v.y;
+      }
+      float rho[2], u[2];
+      march_update<float>(fv, nbP, fl, warp_edge, ph, rho, u);
+      if (t < n_own) {
+        if (!warp_border) {
+#pragma unroll
+          for (int i = 0; i < 9; ++i) Pop<float>::st2(fo, pslot(g, i, k), fv[0][i], fv[1][i], 0.0f, 0.0f);
+          if (warp_edge) store_bounced_near(fo, g, k, fl, fv, zr);
+        } else {
+          const int x = x0 - 1 + col, y = y0 - 1 + row;
+          store_node(fo, g, x, y, k, fv, zr);
+          store_bounced(fo, g, x, y, fl, fv, zr);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i) s[i * TILE_RS + slot] = make_float2(fv[0][i], fv[1][i]);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_own; t += TMA_THREADS) {
+      const uint16_t e = __ldg(entries + e0 + t);
+      const int slot = e & TE_SLOT;
+      const int row = slot / TILE_RW, col = slot - row * TILE_RW;
+      const int k = korg + row * g.px + col;
+      const uint16_t fl = (e & TE_SOLIDNB) ? __ldg(flags + k) : uint16_t(0);
+      float fn[2][9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const bool bounce = i != 0 && (fl & nb_bit(opp_of(i)));
+        const V v = bounce ? s[opp_of(i) * TILE_RS + slot] : s[i * TILE_RS + slot - cx_of(i) - cy_of(i) * TILE_RW];
+        fn[0][i] = v.x;
+        fn[1][i] = v.y;
+      }
+      const float r0 = density(fn[0]), r1 = density(fn[1]);
+      stP(Po, k, r0, r1);
+      if (e & TE_BORDER) {
+        const int x = x0 - 1 + col, y = y0 - 1 + row;
+        for_ghost_images(g, x, y, [&](int kk) { stP(Po, kk, r0, r1); });
+      }
+    }
+    __syncthreads();  // this tile's buffer and the f*(t+1) region are free
+  }
+}
+
+}  // namespace lbm

@@ -20,7 +20,7 @@ OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_SPACE, ERR_TIMEOUT = range(6)
 WET_MARTYS_CHEN, WET_LLKC, WET_VIRTUAL_AVG, WET_CONSTANT = range(4)
 PAIR_CROSS, PAIR_SELF = 0, 1
 STORAGE = {"fp32": 0, "fp64": 1, "fp16": 2, "bf16": 3}
-KERNEL = {"auto": 0, "two_pass": 1, "fused": 2, "tiled": 3, "halo": 4}
+KERNEL = {"auto": 0, "two_pass": 1, "fused": 2, "tiled": 3, "halo": 4, "tma": 5}
 WETTING = {"martys_chen": 0, "mc": 0, "llkc": 1, "virtual_avg": 2, "improved": 2, "constant": 3}
 
 
@@ -31,6 +31,7 @@ class LbmParams(ctypes.Structure):
         ("tau", ctypes.c_double * 2), ("G_AB", ctypes.c_double),
         ("storage", ctypes.c_int32), ("kernel", ctypes.c_int32),
         ("rho_ref", ctypes.c_double * 2), ("max_interface", ctypes.c_int64),
+        ("velocity_refs", ctypes.c_int32),
     ]
 
 
@@ -66,10 +67,11 @@ EXPORTS = [
     "lbm_workspace_bytes", "lbm_create", "lbm_set_stream", "lbm_set_geometry", "lbm_set_wetting",
     "lbm_init_fields", "lbm_step", "lbm_step_profiled", "lbm_moments", "lbm_forces", "lbm_get_populations",
     "lbm_set_populations", "lbm_mass", "lbm_diagnostics", "lbm_set_l2_fetch_granularity", "lbm_interface_count",
-    "lbm_sync", "lbm_run_host",
+    "lbm_sync", "lbm_run_host", "lbm_run_host_f32",
     "lbm_destroy", "lbm_status_str", "lbm_last_error", "lbm_launch_count",
     "lbm_batch_workspace_bytes", "lbm_batch_create", "lbm_batch_set_graph_steps", "lbm_batch_step",
-    "lbm_batch_autotune", "lbm_batch_launch_count", "lbm_batch_last_error", "lbm_batch_destroy",
+    "lbm_batch_autotune", "lbm_batch_set_schedule", "lbm_batch_config", "lbm_batch_launch_count",
+    "lbm_batch_last_error", "lbm_batch_destroy",
 ]
 
 _lock = threading.Lock()
@@ -121,6 +123,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "lbm_interface_count": [vp, ctypes.POINTER(i64)],
             "lbm_sync": [vp],
             "lbm_run_host": [vp, W, vp, vp, vp, i32, vp, vp, vp, vp],
+            "lbm_run_host_f32": [vp, W, vp, vp, vp, i32, vp, vp, vp, vp],
             "lbm_destroy": [vp],
         }
         for name, args in sig.items():
@@ -140,6 +143,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "lbm_batch_set_graph_steps": [vp, i32],
             "lbm_batch_step": [vp, i32],
             "lbm_batch_autotune": [vp, i32, ctypes.POINTER(i32)],
+            "lbm_batch_set_schedule": [vp, i32],
+            "lbm_batch_config": [vp, ctypes.POINTER(i32)],
             "lbm_batch_destroy": [vp],
         }.items():
             fn = getattr(lib, name)
@@ -169,7 +174,8 @@ def set_l2_fetch_granularity(nbytes: int) -> int:
 
 
 def make_params(nx, ny, *, tau=(1.0, 1.0), G_AB=3.0, periodic_x=False, periodic_y=False,
-                storage="fp32", kernel="auto", rho_ref=(1.0, 1.0), max_interface=0) -> LbmParams:
+                storage="fp32", kernel="auto", rho_ref=(1.0, 1.0), max_interface=0,
+                velocity_refs=False) -> LbmParams:
     """lbm_params of the C ABI. kernel: "auto" (tiled for fp32/fp64, two-pass
     for fp16/bf16), "two_pass", "fused" (marching single pass, fp32/fp64) or
     "tiled"; every schedule gives the same results bit for bit."""
@@ -182,6 +188,7 @@ def make_params(nx, ny, *, tau=(1.0, 1.0), G_AB=3.0, periodic_x=False, periodic_
     p.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
     p.rho_ref[0], p.rho_ref[1] = rho_ref
     p.max_interface = int(max_interface)
+    p.velocity_refs = int(bool(velocity_refs))
     return p
 
 
@@ -353,6 +360,20 @@ class Simulation:
         self._check(self.lib.lbm_run_host(self.h, ctypes.byref(wetting), hp(mask), hp(rhoA), hp(rhoB),
                                           int(nsteps), *[hp(o) for o in outs]), "lbm_run_host")
 
+    def run_host_f32(self, wetting: LbmWetting, mask, rhoA, rhoB, nsteps, outputs=None):
+        """run_host with FP32 host arrays (densities in; rho^A, rho^B, u_x,
+        u_y out): half the transfer bytes (lbm_run_host_f32)."""
+        def hp(a):
+            if a is None:
+                return None
+            if isinstance(a, np.ndarray):
+                assert a.dtype in (np.float32, np.uint8)
+                return a.ctypes.data
+            return a.data_ptr()
+        outs = outputs if outputs is not None else [None] * 4
+        self._check(self.lib.lbm_run_host_f32(self.h, ctypes.byref(wetting), hp(mask), hp(rhoA), hp(rhoB),
+                                              int(nsteps), *[hp(o) for o in outs]), "lbm_run_host_f32")
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.lbm_destroy(self.h)
@@ -407,6 +428,19 @@ class Batch:
         ch = (ctypes.c_int32 * 2)()
         self._check(self.lib.lbm_batch_autotune(self.h, int(trial_steps), ch), "lbm_batch_autotune")
         return int(ch[0]), int(ch[1])
+
+    def set_schedule(self, kernel):
+        """"two_pass" (default) or "tiled" (4-/8-byte storage)."""
+        self._check(self.lib.lbm_batch_set_schedule(self.h, KERNEL[kernel] if isinstance(kernel, str) else int(kernel)),
+                    "lbm_batch_set_schedule")
+        return self
+
+    def config(self):
+        """(schedule name, threads per block, steps per graph replay)."""
+        c = (ctypes.c_int32 * 3)()
+        self._check(self.lib.lbm_batch_config(self.h, c), "lbm_batch_config")
+        names = {v: k for k, v in KERNEL.items()}
+        return names[c[0]], int(c[1]), int(c[2])
 
     @property
     def launch_count(self):

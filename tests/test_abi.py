@@ -133,7 +133,7 @@ def test_tiled_schedule_workspace_without_gpu():
             tiled = lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="tiled"))
             assert tiled - base == extra + 2 * plane * 4, (nx, ny, st)
     with pytest.raises(lbm.LbmError):
-        lbm.workspace_bytes(lbm.make_params(8, 8, kernel=5))
+        lbm.workspace_bytes(lbm.make_params(8, 8, kernel=6))
 
 
 def test_halo_schedule_workspace_without_gpu():

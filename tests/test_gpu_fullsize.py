@@ -65,7 +65,7 @@ def _windows(mask, rA, count=4, seed=7):
 @pytest.mark.parametrize("storage,kernel,tol", [("fp32", "two_pass", 1e-6), ("fp16", "auto", 2.5e-4),
                                                 ("bf16", "auto", 2.5e-3), ("fp32", "fused", 1e-6),
                                                 ("fp32", "tiled", 1e-6), ("fp16", "tiled", 2.5e-4),
-                                                ("fp32", "halo", 1e-6)])
+                                                ("fp32", "halo", 1e-6), ("fp32", "tma", 1e-6)])
 def test_full_size_step_matches_oracle_on_windows(workload, storage, kernel, tol):
     mask, rA, rB = workload
     wins = _windows(mask, rA)

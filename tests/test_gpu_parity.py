@@ -22,7 +22,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 from paper_2009_12584_gb300 import lbm  # noqa: E402
 
-KERNELS = ["two_pass", "fused", "tiled", "halo"]
+KERNELS = ["two_pass", "fused", "tiled", "halo", "tma"]
 
 WETTINGS = {
     "mc": (dict(bc=oracle.BC_MARTYS_CHEN, G_s=(-0.2, 0.2)), ("martys_chen", dict(G_s=(-0.2, 0.2)))),
@@ -260,6 +260,27 @@ def test_run_host_matches_device_path():
     assert np.array_equal(outs[2], u[0].cpu().numpy())
 
 
+def test_run_host_f32_matches_device_path():
+    """The FP32 host interface starts from the FP32-rounded densities and
+    returns the FP32-rounded moments of the same run (FP32 storage computes
+    in FP32, so the rounding of the outputs is exact)."""
+    nx, ny = 90, 60
+    mask = inputs.inclined_wall_mask(nx, ny, 20.0, 10)
+    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, ny / 2, 10)
+    rA32, rB32 = rA.astype(np.float32), rB.astype(np.float32)
+    a = lbm.Simulation(nx, ny)
+    a.set_geometry(mask).set_wetting("llkc", G_s=(-0.5, 0.5))
+    a.init_fields(rA32.astype(np.float64), rB32.astype(np.float64)).step(40)
+    rhoA, rhoB, u = a.moments()
+    b = lbm.Simulation(nx, ny)
+    outs = [np.zeros((ny, nx), np.float32) for _ in range(4)]
+    b.run_host_f32(lbm.make_wetting("llkc", G_s=(-0.5, 0.5)), mask.copy(), rA32, rB32, 40, outs)
+    assert np.array_equal(outs[0], rhoA.cpu().numpy().astype(np.float32))
+    assert np.array_equal(outs[1], rhoB.cpu().numpy().astype(np.float32))
+    assert np.array_equal(outs[2], u[0].cpu().numpy().astype(np.float32))
+    assert np.array_equal(outs[3], u[1].cpu().numpy().astype(np.float32))
+
+
 def test_errors_are_status_codes():
     nx, ny = 16, 16
     with pytest.raises(lbm.LbmError) as e:
@@ -281,28 +302,9 @@ def test_errors_are_status_codes():
     assert e.value.status == lbm.ERR_SPACE
 
 
-# Reduced-precision storage: populations stored as FP16/BF16 deviations from
-# w_i times the density of the node that wrote them (FP32 arithmetic). The
-# bounds below are about 5x the errors measured on GB300 at this size.
-REDUCED_TOL = {"fp16": dict(rho=5e-3, u=2e-4, mass=5e-4), "bf16": dict(rho=0.1, u=2e-3, mass=1e-2)}
-
-
+@pytest.mark.parametrize("vref", [False, True], ids=["rho_refs", "velocity_refs"])
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
-@pytest.mark.parametrize("wet", ["mc", "improved"])
-def test_reduced_storage_inclined_wall(storage, wet):
-    nx, ny = 200, 100
-    mask = inputs.inclined_wall_mask(nx, ny, 20.0, 15)
-    rA, rB = inputs.sharp_droplet(nx, ny, nx / 2, ny / 2, 15)
-    o, sim, g = run_pair(nx, ny, mask, rA, rB, 1000, wet, storage=storage)
-    d_rho, d_u = errors(o, g, mask)
-    tol = REDUCED_TOL[storage]
-    assert d_rho <= tol["rho"] and d_u <= tol["u"], (d_rho, d_u)
-    m = sim.mass()
-    assert np.all(np.abs(m - o.mass()) / o.mass() <= tol["mass"]), (m, o.mass())
-
-
-@pytest.mark.parametrize("storage", ["fp16", "bf16"])
-def test_reduced_storage_checkpoint_roundtrip(storage):
+def test_reduced_storage_checkpoint_roundtrip(storage, vref):
     """Populations written back through lbm_set_populations are re-encoded
     relative to each node's own density and read back to the precision of
     the format."""
@@ -312,7 +314,7 @@ def test_reduced_storage_checkpoint_roundtrip(storage):
     a = lbm.Simulation(nx, ny, periodic_x=True, periodic_y=True, storage="fp64")
     a.set_geometry(mask).set_wetting("llkc", G_s=(-0.5, 0.5)).init_fields(rA, rB, ux, uy).step(5)
     f = a.populations()
-    b = lbm.Simulation(nx, ny, periodic_x=True, periodic_y=True, storage=storage)
+    b = lbm.Simulation(nx, ny, periodic_x=True, periodic_y=True, storage=storage, velocity_refs=vref)
     b.set_geometry(mask).set_wetting("llkc", G_s=(-0.5, 0.5)).set_populations(f)
     eps = 2.0 ** -11 if storage == "fp16" else 2.0 ** -8
     # deviations are a few percent of f at most here
@@ -345,6 +347,63 @@ def test_batch_matches_individual_runs(storage):
     assert b.launch_count > 0
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp64"])
+def test_batch_tiled_schedule_matches_individual_runs(storage):
+    """The batched tiled schedule (one Eq. 8 launch and one tiled launch over
+    all members' tiles per step) leaves every member bit-identical to the
+    same simulation stepped alone, with direct launches and graph replays."""
+    work = inputs.batched_workload(7, seed=3, size_scale=0.3)
+    def make():
+        sims = []
+        for w in work:
+            s = lbm.Simulation(w["nx"], w["ny"], storage=storage)
+            s.set_geometry(w["mask"]).set_wetting(w["bc"], **w["wetting"]).init_fields(w["rhoA"], w["rhoB"])
+            sims.append(s)
+        return sims
+    solo = make()
+    for s in solo:
+        s.step(41)
+    group = make()
+    b = lbm.Batch(group).set_schedule("tiled")
+    assert b.config()[0] == "tiled"
+    b.step(5)             # direct launches
+    b.set_graph_steps(8)
+    b.step(32)            # four graph replays
+    b.set_schedule("two_pass")
+    b.step(4)             # switching schedules keeps the state
+    for a, c in zip(solo, group):
+        assert torch.equal(a.populations(), c.populations())
+        assert np.array_equal(a.mass(), c.mass())
+
+
+@pytest.mark.parametrize("schedule", ["two_pass", "tiled"])
+def test_batch_members_match_oracle(schedule):
+    """Members of one batch (different sizes, wall angles and wetting
+    schemes) compared directly with their own oracle runs: FP64 storage
+    within rounding order (1e-11 relative density, 1e-12 velocity)."""
+    work = inputs.batched_workload(5, seed=21, size_scale=0.2)
+    sims = []
+    for w in work:
+        s = lbm.Simulation(w["nx"], w["ny"], storage="fp64")
+        s.set_geometry(w["mask"]).set_wetting(w["bc"], **w["wetting"]).init_fields(w["rhoA"], w["rhoB"])
+        sims.append(s)
+    b = lbm.Batch(sims).set_schedule(schedule)
+    b.set_graph_steps(8)
+    b.step(60)
+    bcs = {"martys_chen": oracle.BC_MARTYS_CHEN, "llkc": oracle.BC_LLKC, "virtual_avg": oracle.BC_VIRTUAL_AVG}
+    assert len({w["bc"] for w in work}) >= 2
+    for i in (0, 2, 4):
+        w = work[i]
+        o = oracle.Oracle(w["nx"], w["ny"], w["mask"], bc=bcs[w["bc"]], **w["wetting"]).init(w["rhoA"], w["rhoB"])
+        o.step(60)
+        rA, rB, u = (v.cpu().numpy() for v in sims[i].moments())
+        rho_o, _, _, u_o = o.fields()
+        fl = w["mask"] == 0
+        assert np.abs(rA - rho_o[0])[fl].max() / rho_o[0][fl].min() < 1e-11, i
+        assert np.abs(rB - rho_o[1])[fl].max() / rho_o[1][fl].min() < 1e-11, i
+        assert np.abs(u - u_o)[:, fl].max() < 1e-12, i
+
+
 def test_batch_autotune_and_members_stay_usable():
     work = inputs.batched_workload(5, seed=4, size_scale=0.25)
     sims = []
@@ -356,6 +415,7 @@ def test_batch_autotune_and_members_stay_usable():
     b = lbm.Batch(sims)
     threads, steps = b.autotune(8)
     assert threads in (128, 256) and steps in (2, 8, 32)
+    assert b.config()[0] in ("two_pass", "tiled") and b.config()[2] == steps
     b.step(10)
     for s, m in zip(sims, m0):
         np.testing.assert_allclose(s.mass(), m, rtol=1e-5)
@@ -403,10 +463,11 @@ def test_geometry_change_rebuilds_lists(kernel):
     assert np.array_equal(a.mass(), b.mass())
 
 
+@pytest.mark.parametrize("vref", [False, True], ids=["rho_refs", "velocity_refs"])
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
 @pytest.mark.parametrize("wet", ["mc", "improved", "improved_self_d2q9"])
 @pytest.mark.parametrize("case", ["porous_periodic", "wall_walled"])
-def test_tiled_16bit_matches_two_pass_bitwise(storage, wet, case):
+def test_tiled_16bit_matches_two_pass_bitwise(storage, wet, case, vref):
     """With 16-bit storage the tiled kernel decodes with the writers'
     densities of the step before, encodes with its own, and sums the values
     the next step decodes: the same bits as the two-pass schedule. The tiled
@@ -423,7 +484,8 @@ def test_tiled_16bit_matches_two_pass_bitwise(storage, wet, case):
     _, (kind, gkw) = WETTINGS[wet]
     outs = []
     for kernel in ("two_pass", "tiled"):
-        s = lbm.Simulation(nx, ny, periodic_x=per[0], periodic_y=per[1], storage=storage, kernel=kernel)
+        s = lbm.Simulation(nx, ny, periodic_x=per[0], periodic_y=per[1], storage=storage, kernel=kernel,
+                           velocity_refs=vref)
         s.set_geometry(mask).set_wetting(kind, **gkw).init_fields(rA, rB).step(13)
         s.moments()
         s.step(24)
