@@ -299,12 +299,15 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_single(n, mask, rA, rB, nf, storage, kernel, steps, warmup, l2_fetch):
-    """The throughput workload with another population storage."""
+def run_single(n, mask, rA, rB, nf, storage, kernel, steps, warmup, l2_fetch, velocity_refs=False):
+    """The throughput workload with another population storage (16-bit
+    storage: velocity_refs selects the encoding relative to the writer's
+    momentum, lbm_params.velocity_refs)."""
     import torch
     from paper_2009_12584_gb300 import lbm
     l2_prev = lbm.set_l2_fetch_granularity(l2_fetch) if l2_fetch else None
-    sim = lbm.Simulation(n, n, periodic_x=True, periodic_y=True, storage=storage, kernel=kernel)
+    sim = lbm.Simulation(n, n, periodic_x=True, periodic_y=True, storage=storage, kernel=kernel,
+                         velocity_refs=velocity_refs)
     sim.set_geometry(mask).set_wetting("virtual_avg", G_s=(3.0, 3.0), chi=chi_from_xi(XI)).init_fields(rA, rB)
     sim.step(warmup)
     torch.cuda.synchronize()
@@ -548,9 +551,12 @@ def main():
     if rank == 0 and not args.no_extra:
         del sim
         torch.cuda.empty_cache()
-        for st in ("fp16", "bf16"):
-            extra[st] = run_single(n, mask, rA, rB, nf, st, args.kernel, args.steps, args.warmup,
-                                   l2_fetch_for(args.kernel, st, args.l2_fetch))
+        # 16-bit storage, both encodings ("u": relative to the writer's
+        # momentum, the encoding that holds the accuracy bounds)
+        for st in ("fp16", "bf16", "fp16u", "bf16u"):
+            base = st.rstrip("u")
+            extra[st] = run_single(n, mask, rA, rB, nf, base, args.kernel, args.steps, args.warmup,
+                                   l2_fetch_for(args.kernel, base, args.l2_fetch), velocity_refs=st.endswith("u"))
         for st in ("fp32", "fp16"):
             extra[f"batched_{st}"] = run_batched(st, args.steps, args.warmup)
         extra["err_vs_oracle"] = accuracy()

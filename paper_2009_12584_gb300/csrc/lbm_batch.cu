@@ -23,7 +23,7 @@ template <typename C>
 struct BatchDesc {
   const void* f[2];
   void* Pbuf[2];
-  __half2* Ubuf[2];  // 16-bit storage: velocity part of the references of f[0] / f[1]
+  UPair* Ubuf[2];  // 16-bit storage: velocity part of the references of f[0] / f[1]
   const uint16_t* flags;
   const uint16_t* tile_entries;  // tiled schedule: the member's per-tile lists
   const int* tile_off;
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MINB)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_collide_batch(const BatchDesc<typename Pop<T>::C>* __restrict__ d,
+__global__ void __launch_bounds__(256, 4) k_collide_batch(const BatchDesc<typename Pop<T>::C>* __restrict__ d,
                                                        const int2* __restrict__ blk, int parity) {
   using C = typename Pop<T>::C;
   const int2 b = blk[blockIdx.x];

@@ -121,8 +121,9 @@ __device__ __forceinline__ void stP_ghosts(C* __restrict__ P, const Geo& g, int 
 
 // ---------------------------------------------------------------------------
 // Population storage. FP32/FP64 store f itself. FP16/BF16 store the
-// deviation f - w_i rho_ref^sigma, which keeps the rest-state part exact and
-// spends the 11/8 significand bits on what varies.
+// deviation of f from a reference its writer and reader both know (see
+// pull_refs), which keeps the rest-state part exact and spends the 11/8
+// significand bits on what varies.
 //
 // Layout: nine planes of component pairs. The populations of components A
 // and B for direction i at padded index k are adjacent, at element
@@ -166,24 +167,29 @@ struct Pop<double> {
     *reinterpret_cast<double2*>(p + j) = make_double2(a, b);
   }
 };
+// FP16 keeps the deviation times 2^12 (exact: a power of two), so that the
+// small deviations left by the references stay out of FP16's subnormal range
+// (below 2^-14), where precision would be absolute instead of relative;
+// deviations up to 16 in magnitude fit.
+constexpr float HALF_SCALE = 4096.0f, HALF_UNSCALE = 1.0f / 4096.0f;
 template <>
 struct Pop<__half> {
   using C = float;
   static __device__ __forceinline__ float ld(const __half* p, int64_t k, float ref) {
-    return __half2float(p[k]) + ref;
+    return fmaf(__half2float(p[k]), HALF_UNSCALE, ref);
   }
   static __device__ __forceinline__ void st(__half* p, int64_t k, float v, float ref) {
-    p[k] = __float2half_rn(v - ref);
+    p[k] = __float2half_rn((v - ref) * HALF_SCALE);
   }
-  static __device__ __forceinline__ __half enc(float v, float ref) { return __float2half_rn(v - ref); }
-  static __device__ __forceinline__ float dec(__half v, float ref) { return __half2float(v) + ref; }
+  static __device__ __forceinline__ __half enc(float v, float ref) { return __float2half_rn((v - ref) * HALF_SCALE); }
+  static __device__ __forceinline__ float dec(__half v, float ref) { return fmaf(__half2float(v), HALF_UNSCALE, ref); }
   static __device__ __forceinline__ void ld2(const __half* p, int64_t j, float ra, float rb, float& a, float& b) {
     const __half2 v = __ldg(reinterpret_cast<const __half2*>(p + j));
-    a = __low2float(v) + ra;
-    b = __high2float(v) + rb;
+    a = fmaf(__low2float(v), HALF_UNSCALE, ra);
+    b = fmaf(__high2float(v), HALF_UNSCALE, rb);
   }
   static __device__ __forceinline__ void st2(__half* p, int64_t j, float a, float b, float ra, float rb) {
-    *reinterpret_cast<__half2*>(p + j) = __floats2half2_rn(a - ra, b - rb);
+    *reinterpret_cast<__half2*>(p + j) = __floats2half2_rn((a - ra) * HALF_SCALE, (b - rb) * HALF_SCALE);
   }
 };
 template <>

@@ -12,6 +12,7 @@
 
 using lbm::Geo;
 using lbm::Phys;
+using lbm::UPair;
 
 struct lbm_ctx {
   // TMA schedule: tensor maps of the population buffers f[0], f[1] (rank 3:
@@ -34,7 +35,7 @@ struct lbm_ctx {
   void* Pbuf[3];       // density plane pairs (compute type); the third only for
                        // the tiled schedule with 16-bit storage (null otherwise)
   char* Pbase;         // start of the density planes in the workspace
-  __half2* Ubuf[2];    // 16-bit storage with velocity_refs: 3 u of the writers of f[0] / f[1] (the
+  UPair* Ubuf[2];    // 16-bit storage with velocity_refs: 3 u of the writers of f[0] / f[1] (the
                        // velocity part of the encoding references); null otherwise
   void* P;             // Pbuf[pcur]: the densities the current populations were
                        // written with (16-bit encoding references); after a

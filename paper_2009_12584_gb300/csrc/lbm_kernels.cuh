@@ -35,16 +35,43 @@ __device__ __forceinline__ void prefetch_list_ahead(const int* __restrict__ list
 }
 
 // Encoding references of 16-bit storage. A 2-byte population travelling
-// along c_d is stored as its deviation from w_d rho (1 + c_d . U), the part
-// of its writer's equilibrium (Eq. 2) that is linear in u, with rho and
-// U = 3 u (rounded to FP16) of the node that wrote it, taken when it
-// collided. rho is kept in the reference density plane Pref and U in the
-// velocity plane Uref, so that the reader forms the same reference; the
-// deviation is then the non-equilibrium part and the O(u^2) terms, and the
-// 11 (FP16) or 8 (BF16) significand bits go to what varies. For 4- and
+// along c_d is stored as its deviation from a reference its writer and its
+// reader both know, taken from the node that wrote it when it collided:
+//  - by default w_d rho^s of the writer (density plane Pref): the deviation
+//    is the velocity and non-equilibrium part, a few percent of f;
+//  - with velocity references (lbm_params.velocity_refs), w_d rho^s
+//    (1 + c_d . U^s) with U^s = 3 j*^s / rho^s, j*^s the momentum of the
+//    populations the writer stored (post-collision), rounded to FP16 and
+//    kept in a velocity plane Uref: the reference then carries the first
+//    moment of what was written (the equilibrium's velocity term and the
+//    Guo source's first-order term), and the deviation only the rest.
+// The 11 (FP16) or 8 (BF16) significand bits go to what varies. For 4- and
 // 8-byte storage the references are zero and the planes are not read.
 template <typename T>
 constexpr bool kDev = sizeof(T) == 2;
+
+// Element of a velocity plane: (U^A, U^B) as two FP16 pairs.
+using UPair = uint2;
+struct UVal {
+  float2 v[2];  // U^A, U^B
+};
+__device__ __forceinline__ UVal u_unpack(UPair p) {
+  UVal u;
+  u.v[0] = __half22float2(*reinterpret_cast<const __half2*>(&p.x));
+  u.v[1] = __half22float2(*reinterpret_cast<const __half2*>(&p.y));
+  return u;
+}
+// U^s = 3 j^s / rho^s of both components, rounded to FP16 (jx, jy, rho:
+// component A in .x, B in .y).
+__device__ __forceinline__ UPair u_pack(float2 jx, float2 jy, float2 rho) {
+  const float ia = rho.x > 0.0f ? 3.0f / rho.x : 0.0f, ib = rho.y > 0.0f ? 3.0f / rho.y : 0.0f;
+  const __half2 a = __floats2half2_rn(jx.x * ia, jy.x * ia);
+  const __half2 b = __floats2half2_rn(jx.y * ib, jy.y * ib);
+  UPair p;
+  p.x = *reinterpret_cast<const unsigned*>(&a);
+  p.y = *reinterpret_cast<const unsigned*>(&b);
+  return p;
+}
 
 // c_d . U as a fixed sequence of FP32 operations; for -c_d it gives the
 // exact negation (round to nearest is symmetric).
@@ -62,27 +89,37 @@ __device__ __forceinline__ float ref_of(int i, float rho, float cu) {
   return fmaf(wr, cu, wr);
 }
 
-// The velocity part U = 3 u of a node's references, as stored (FP16).
-__device__ __forceinline__ __half2 u_ref(float ux, float uy) { return __floats2half2_rn(3.0f * ux, 3.0f * uy); }
-
 // References of the 18 populations pulled at padded index k: the writer of
 // slot i is x - c_i (direction i), or x itself when x - c_i is solid (its
 // bounced slot, which holds the value it sent along -c_i). check: whether fl
-// may hold solid neighbours.
+// may hold solid neighbours. Uref: the velocity plane, or null.
 template <typename T, typename C>
-__device__ __forceinline__ void pull_refs(const C* __restrict__ Pref, const __half2* __restrict__ Uref, const Geo& g,
+__device__ __forceinline__ void pull_refs(const C* __restrict__ Pref, const UPair* __restrict__ Uref, const Geo& g,
                                           int k, uint16_t fl, bool check, C ref[2][9]) {
   if constexpr (kDev<T>) {
+    if (Uref) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const bool self = i == 0 || (check && (fl & nb_bit(opp_of(i))));
-      const int m = self ? k : k - cx_of(i) - cy_of(i) * g.px;
-      C a, b;
-      ldP(Pref, m, a, b);
-      const float cd = Uref ? cdot(i, __half22float2(__ldg(Uref + m))) : 0.0f;  // no velocity plane: w_i rho
-      const float cu = (self && i != 0) ? -cd : cd;
-      ref[0][i] = ref_of(i, a, cu);
-      ref[1][i] = ref_of(i, b, cu);
+      for (int i = 0; i < 9; ++i) {
+        const bool self = i == 0 || (check && (fl & nb_bit(opp_of(i))));
+        const int m = self ? k : k - cx_of(i) - cy_of(i) * g.px;
+        C a, b;
+        ldP(Pref, m, a, b);
+        const UVal u = u_unpack(__ldg(Uref + m));
+        const bool back = self && i != 0;  // the value was sent along -c_i
+        const float ca = cdot(i, u.v[0]), cb = cdot(i, u.v[1]);
+        ref[0][i] = ref_of(i, a, back ? -ca : ca);
+        ref[1][i] = ref_of(i, b, back ? -cb : cb);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const bool self = i == 0 || (check && (fl & nb_bit(opp_of(i))));
+        const int m = self ? k : k - cx_of(i) - cy_of(i) * g.px;
+        C a, b;
+        ldP(Pref, m, a, b);
+        ref[0][i] = w_of<C>(i) * a;
+        ref[1][i] = w_of<C>(i) * b;
+      }
     }
   } else {
 #pragma unroll
@@ -92,27 +129,37 @@ __device__ __forceinline__ void pull_refs(const C* __restrict__ Pref, const __ha
   }
 }
 
-// References for what a node writes, given its own rho and U (as stored):
-// ref[s][i] for its slot i (direction i). Its bounced slot i holds the value
-// sent along -c_i, whose reference is ref[s][opp(i)].
+// References for what a node writes, given its own rho and (with velocity
+// references, vref) its U as stored: ref[s][i] for its slot i (direction
+// i). Its bounced slot i holds the value sent along -c_i, whose reference
+// is ref[s][opp(i)].
 template <typename T, typename C>
-__device__ __forceinline__ void write_refs(const C rho[2], float2 U, C ref[2][9]) {
+__device__ __forceinline__ void write_refs(const C rho[2], bool vref, const UVal& U, C ref[2][9]) {
+  if constexpr (kDev<T>) {
+    if (vref) {
 #pragma unroll
-  for (int s = 0; s < 2; ++s)
+      for (int s = 0; s < 2; ++s)
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      if constexpr (kDev<T>)
-        ref[s][i] = ref_of(i, rho[s], cdot(i, U));
-      else
-        ref[s][i] = C(0);
+        for (int i = 0; i < 9; ++i) ref[s][i] = ref_of(i, rho[s], cdot(i, U.v[s]));
+    } else {
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ref[s][i] = w_of<C>(i) * rho[s];
     }
+  } else {
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int i = 0; i < 9; ++i) ref[s][i] = C(0);
+  }
 }
 
 // ---- K1: densities --------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(128) k_density(const T* __restrict__ f, typename Pop<T>::C* __restrict__ P,
                                                  const typename Pop<T>::C* __restrict__ Pref,
-                                                 const __half2* __restrict__ Uref,
+                                                 const UPair* __restrict__ Uref,
                                                  const uint16_t* __restrict__ flags, Geo g,
                                                  PhysK<typename Pop<T>::C> ph) {
   using C = typename Pop<T>::C;
@@ -146,7 +193,7 @@ __device__ __forceinline__ void coords(const Geo& g, int k, int& x, int& y) {
 template <typename T>
 __device__ __forceinline__ void density_node(const T* __restrict__ f, typename Pop<T>::C* __restrict__ P,
                                              const typename Pop<T>::C* __restrict__ Pref,
-                                             const __half2* __restrict__ Uref,
+                                             const UPair* __restrict__ Uref,
                                              const uint16_t* __restrict__ flags, const int* __restrict__ list, int t,
                                              const Geo& g) {
   using C = typename Pop<T>::C;
@@ -175,7 +222,7 @@ __device__ __forceinline__ void density_node(const T* __restrict__ f, typename P
 template <typename T>
 __global__ void __launch_bounds__(256) k_density_list(const T* __restrict__ f, typename Pop<T>::C* __restrict__ P,
                                                       const typename Pop<T>::C* __restrict__ Pref,
-                                                      const __half2* __restrict__ Uref,
+                                                      const UPair* __restrict__ Uref,
                                                       const uint16_t* __restrict__ flags,
                                                       const int* __restrict__ list, int nfluid, Geo g,
                                                       PhysK<typename Pop<T>::C> ph) {
@@ -188,7 +235,7 @@ __global__ void __launch_bounds__(256) k_density_list(const T* __restrict__ f, t
 template <typename T>
 __device__ __forceinline__ void collide_node_pair(const T* __restrict__ f, T* __restrict__ fo,
                                                   const float* __restrict__ P, const float* __restrict__ Pref,
-                                                  const __half2* __restrict__ Uref, __half2* __restrict__ Uo,
+                                                  const UPair* __restrict__ Uref, UPair* __restrict__ Uo,
                                                   const uint16_t* __restrict__ flags, unsigned e, bool warp_edge,
                                                   bool warp_border, const Geo& g, const PhysK<float>& ph) {
   const int k = (int)(e & ~LIST_TAGS);
@@ -210,20 +257,24 @@ __device__ __forceinline__ void collide_node_pair(const T* __restrict__ f, T* __
   float ux, uy;
   const float2 rho = warp_edge ? update_pair<true>(fp, q, fl, ph, ux, uy) : update_pair<false>(fp, q, fl, ph, ux, uy);
   const float rr[2] = {rho.x, rho.y};
-  float2 U = make_float2(0.0f, 0.0f);
+  UVal U{};
   if constexpr (kDev<T>) {
     if (Uo) {
-    const __half2 uh = u_ref(ux, uy);
-    U = __half22float2(uh);
-    Uo[k] = uh;
-    if (warp_border) {
-      int x, y;
-      coords(g, k, x, y);
-      for_ghost_images(g, x, y, [&](int kk) { Uo[kk] = uh; });
-    }
+      // momentum of each component's post-collision populations
+      const float2 d57 = sub2(fp[5], fp[7]), d86 = sub2(fp[8], fp[6]);
+      const float2 jx = add2(sub2(fp[1], fp[3]), add2(d57, d86));
+      const float2 jy = add2(sub2(fp[2], fp[4]), sub2(d57, d86));
+      const UPair up = u_pack(jx, jy, rho);
+      U = u_unpack(up);
+      Uo[k] = up;
+      if (warp_border) {
+        int x, y;
+        coords(g, k, x, y);
+        for_ghost_images(g, x, y, [&](int kk) { Uo[kk] = up; });
+      }
     }
   }
-  write_refs<T>(rr, U, ref);
+  write_refs<T>(rr, Uo != nullptr, U, ref);
   if (!warp_border) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -267,7 +318,7 @@ template <typename T>
 __device__ __forceinline__ void collide_node(const T* __restrict__ f, T* __restrict__ fo,
                                              const typename Pop<T>::C* __restrict__ P,
                                              const typename Pop<T>::C* __restrict__ Pref,
-                                             const __half2* __restrict__ Uref, __half2* __restrict__ Uo,
+                                             const UPair* __restrict__ Uref, UPair* __restrict__ Uo,
                                              const uint16_t* __restrict__ flags, const int* __restrict__ list,
                                              int t, int nfluid, const Geo& g,
                                              const PhysK<typename Pop<T>::C>& ph) {
@@ -303,7 +354,7 @@ __device__ __forceinline__ void collide_node(const T* __restrict__ f, T* __restr
   const C ux = ((jxA + jxB) + C(0.5) * (F[0][0] + F[1][0])) * inv;
   const C uy = ((jyA + jyB) + C(0.5) * (F[0][1] + F[1][1])) * inv;
   collide(fv, rho, ux, uy, F, ph.omega, ph.kF);
-  write_refs<T>(rho, make_float2(0.0f, 0.0f), ref);  // the FP64 compute type stores 8-byte populations
+  write_refs<T>(rho, false, UVal{}, ref);  // the FP64 compute type stores 8-byte populations
   if (!warp_border) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) Pop<T>::st2(fo, pslot(g, i, k), fv[0][i], fv[1][i], ref[0][i], ref[1][i]);
@@ -321,8 +372,8 @@ template <typename T>
 __global__ void __launch_bounds__(COLLIDE_THREADS, 8) k_collide_list(const T* __restrict__ f, T* __restrict__ fo,
                                                          const typename Pop<T>::C* __restrict__ P,
                                                          const typename Pop<T>::C* __restrict__ Pref,
-                                                         const __half2* __restrict__ Uref,
-                                                         __half2* __restrict__ Uo,
+                                                         const UPair* __restrict__ Uref,
+                                                         UPair* __restrict__ Uo,
                                                          const uint16_t* __restrict__ flags,
                                                          const int* __restrict__ list, int nfluid, Geo g,
                                                          PhysK<typename Pop<T>::C> ph) {
@@ -425,7 +476,7 @@ __global__ void __launch_bounds__(128) k_virtual_density(C* __restrict__ P, cons
 template <typename T, int MODE, typename O = double>
 __global__ void __launch_bounds__(128) k_collide(const T* __restrict__ f, const typename Pop<T>::C* __restrict__ P,
                                                  const typename Pop<T>::C* __restrict__ Pref,
-                                                 const __half2* __restrict__ Uref,
+                                                 const UPair* __restrict__ Uref,
                                                  const uint16_t* __restrict__ flags, Geo g,
                                                  PhysK<typename Pop<T>::C> ph, O* __restrict__ out) {
   static_assert(MODE == 1 || MODE == 2, "evaluation modes only");
@@ -477,7 +528,7 @@ static __global__ void k_widen(const float* __restrict__ in, double* __restrict_
 // ---- post-streaming populations out / in ---------------------------------
 template <typename T>
 __global__ void k_get_populations(const T* __restrict__ f, const typename Pop<T>::C* __restrict__ Pref,
-                                  const __half2* __restrict__ Uref,
+                                  const UPair* __restrict__ Uref,
                                   const uint16_t* __restrict__ flags, Geo g,
                                   PhysK<typename Pop<T>::C> ph, double* __restrict__ out) {
   using C = typename Pop<T>::C;
@@ -517,7 +568,7 @@ __device__ __forceinline__ int64_t wrap_compact(const Geo& g, int x, int y) {
 // storage only; u = the momentum of the received populations over their
 // density) are the encoding references of everything the node stores here.
 template <typename T, int SRC>
-__global__ void k_set_state(T* __restrict__ f, typename Pop<T>::C* __restrict__ Pref, __half2* __restrict__ Uo,
+__global__ void k_set_state(T* __restrict__ f, typename Pop<T>::C* __restrict__ Pref, UPair* __restrict__ Uo,
                             const uint16_t* __restrict__ flags, Geo g, PhysK<typename Pop<T>::C> ph,
                             const double* __restrict__ fin, const double* __restrict__ rA,
                             const double* __restrict__ rB, const double* __restrict__ ux,
@@ -563,22 +614,25 @@ __global__ void k_set_state(T* __restrict__ f, typename Pop<T>::C* __restrict__ 
     rho0[s] = r;
   }
   stP_ghosts(Pref, g, x, y, rho0[0], rho0[1]);
-  float2 U = make_float2(0.0f, 0.0f);
-  if (kDev<T> && Uo) {
-    C jx = C(0), jy = C(0);
-    for (int s = 0; s < 2; ++s)
-      for (int j = 1; j < 9; ++j) {
-        const C o = O(n, own, s, j);
-        jx += C(cx_of(j)) * o;
-        jy += C(cy_of(j)) * o;
-      }
-    const C r = rho0[0] + rho0[1];
-    const __half2 uh = u_ref(r > C(0) ? jx / r : C(0), r > C(0) ? jy / r : C(0));
-    U = __half22float2(uh);
-    put_with_ghosts(Uo, g, x, y, uh);
+  UVal U{};
+  if constexpr (kDev<T>) {
+    if (Uo) {
+      // momentum of each component's received populations
+      float j[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+      for (int s = 0; s < 2; ++s)
+        for (int jd = 1; jd < 9; ++jd) {
+          const C o = O(n, own, s, jd);
+          j[s][0] += float(cx_of(jd)) * o;
+          j[s][1] += float(cy_of(jd)) * o;
+        }
+      const UPair up = u_pack(make_float2(j[0][0], j[1][0]), make_float2(j[0][1], j[1][1]),
+                              make_float2(rho0[0], rho0[1]));
+      U = u_unpack(up);
+      put_with_ghosts(Uo, g, x, y, up);
+    }
   }
   C ref[2][9];
-  write_refs<T>(rho0, U, ref);
+  write_refs<T>(rho0, Uo != nullptr, U, ref);
   C fv[2][9];
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
@@ -606,7 +660,7 @@ __global__ void k_set_state(T* __restrict__ f, typename Pop<T>::C* __restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(256) k_mass_partial(const T* __restrict__ f,
                                                       const typename Pop<T>::C* __restrict__ Pref,
-                                                      const __half2* __restrict__ Uref,
+                                                      const UPair* __restrict__ Uref,
                                                       const uint16_t* __restrict__ flags, Geo g,
                                                       PhysK<typename Pop<T>::C> ph, double* __restrict__ partial) {
   using C = typename Pop<T>::C;
@@ -619,13 +673,13 @@ __global__ void __launch_bounds__(256) k_mass_partial(const T* __restrict__ f,
     if (flags[k] & F_SOLID) continue;
     // a node's own slots were written by the node itself
     C rw[2] = {C(0), C(0)};
-    float2 U = make_float2(0.0f, 0.0f);
+    UVal U{};
     if (kDev<T>) {
       ldP(Pref, k, rw[0], rw[1]);
-      if (Uref) U = __half22float2(Uref[k]);
+      if (Uref) U = u_unpack(Uref[k]);
     }
     C ref[2][9];
-    write_refs<T>(rw, U, ref);
+    write_refs<T>(rw, Uref != nullptr, U, ref);
     double r[2] = {0.0, 0.0};
     for (int i = 0; i < 9; ++i) {
       C a, b;

@@ -128,7 +128,7 @@ template <typename T>
 __device__ __forceinline__ void tile_step(int tile, int n_tiles, const T* __restrict__ f, T* __restrict__ fo,
                                           const typename Pop<T>::C* __restrict__ P,
                                           const typename Pop<T>::C* __restrict__ Pref,
-                                          const __half2* __restrict__ Uref, __half2* __restrict__ Uo,
+                                          const UPair* __restrict__ Uref, UPair* __restrict__ Uo,
                                           typename Pop<T>::C* __restrict__ Po, const uint16_t* __restrict__ flags,
                                           const uint16_t* __restrict__ entries, const int* __restrict__ offsets,
                                           const int* __restrict__ nown, const Geo& g, int ntx,
@@ -182,17 +182,23 @@ __device__ __forceinline__ void tile_step(int tile, int n_tiles, const T* __rest
     }
     C rho[2], u[2];
     march_update<C>(fv, nbP, fl, warp_edge, ph, rho, u);
-    float2 U = make_float2(0.0f, 0.0f);
-    if (kDev<T> && Uo) {
-      const __half2 uh = u_ref(u[0], u[1]);
-      U = __half22float2(uh);
-      if (t < n_own) {
-        Uo[k] = uh;
-        if (e & TE_BORDER)
-          for_ghost_images(g, x0 - 1 + col, y0 - 1 + row, [&](int kk) { Uo[kk] = uh; });
+    UVal U{};
+    if constexpr (kDev<T>) {
+      if (Uo) {
+        // momentum of each component's post-collision populations
+        float2 jx, jy;
+        momentum(fv[0], jx.x, jy.x);
+        momentum(fv[1], jx.y, jy.y);
+        const UPair up = u_pack(jx, jy, make_float2(rho[0], rho[1]));
+        U = u_unpack(up);
+        if (t < n_own) {
+          Uo[k] = up;
+          if (e & TE_BORDER)
+            for_ghost_images(g, x0 - 1 + col, y0 - 1 + row, [&](int kk) { Uo[kk] = up; });
+        }
       }
     }
-    write_refs<T>(rho, U, ref);
+    write_refs<T>(rho, Uo != nullptr, U, ref);
     if (t < n_own) {
       if (!warp_border) {
 #pragma unroll
@@ -239,8 +245,8 @@ __device__ __forceinline__ void tile_step(int tile, int n_tiles, const T* __rest
 template <typename T>
 __global__ void __launch_bounds__(TILE_THREADS, TILE_MINB)
     k_tile(const T* __restrict__ f, T* __restrict__ fo, const typename Pop<T>::C* __restrict__ P,
-           const typename Pop<T>::C* __restrict__ Pref, const __half2* __restrict__ Uref,
-           __half2* __restrict__ Uo, typename Pop<T>::C* __restrict__ Po,
+           const typename Pop<T>::C* __restrict__ Pref, const UPair* __restrict__ Uref,
+           UPair* __restrict__ Uo, typename Pop<T>::C* __restrict__ Po,
            const uint16_t* __restrict__ flags,
            const uint16_t* __restrict__ entries, const int* __restrict__ offsets, const int* __restrict__ nown,
            Geo g, int ntx, PhysK<typename Pop<T>::C> ph) {
@@ -256,7 +262,7 @@ constexpr size_t tile_smem() {
 // the kernel's dynamic shared memory limit has been raised.
 template <typename T>
 inline lbm_status launch_tiled(const Geo& g, const Phys& ph, const T* fin, T* fout, const typename Pop<T>::C* P,
-                               const typename Pop<T>::C* Pref, const __half2* Uref, __half2* Uo,
+                               const typename Pop<T>::C* Pref, const UPair* Uref, UPair* Uo,
                                typename Pop<T>::C* Po, const uint16_t* flags,
                                const uint16_t* entries, const int* offsets, const int* nown, bool* smem_set,
                                cudaStream_t stream) {
