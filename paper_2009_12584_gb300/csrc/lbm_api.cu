@@ -39,7 +39,7 @@ bool make_geo(const lbm_params* p, Geo* g) {
 }
 
 struct Layout {
-  size_t f, P, U, flags, list, imask, flist, tent, toff, tnown, hent, hoff, hcnt, hmask, counts, small, partial, mass,
+  size_t f, P, U, flags, list, imask, flist, tent, toff, tcnt, twork, hent, hoff, hcnt, hmask, counts, small, partial, mass,
       smask, stage, dpart, total;
 };
 
@@ -88,7 +88,8 @@ bool layout(const lbm_params* p, const Geo& g, Layout* L) {
   const int64_t nt = uses_tiles(p) ? tile_count(g) : 0;
   L->tent = off;     off = align_up(off + (size_t)nt * TILE_RS * 2, A);
   L->toff = off;     off = align_up(off + (size_t)(nt ? nt + 1 : 0) * 4, A);
-  L->tnown = off;    off = align_up(off + (size_t)nt * 4, A);
+  L->tcnt = off;     off = align_up(off + (size_t)nt * 8, A);
+  L->twork = off;    off = align_up(off + (size_t)(uses_tma(p) ? nt : 0) * 16, A);
   const int64_t nh = uses_halo(p) ? halo_tile_count(g) : 0;
   L->hent = off;     off = align_up(off + (size_t)nh * HALO_RS * 2, A);
   L->hoff = off;     off = align_up(off + (size_t)(nh ? nh + 1 : 0) * 4, A);
@@ -304,10 +305,10 @@ lbm_status step_fused(lbm_ctx* c, int nsteps) {
             c->tma_smem_set = true;
           }
           const int ntx = (c->g.nx + TILE_W - 1) / TILE_W;
-          const int grid = (int)(c->n_tiles < c->num_sms ? c->n_tiles : c->num_sms);
+          const int grid = c->n_work < c->num_sms ? (c->n_work > 0 ? c->n_work : 1) : c->num_sms;
           k_tile_tma<<<grid, TMA_THREADS, SMEM, c->stream>>>(
               c->tmap_f[c->cur], c->tmap_P[c->pcur], (float*)fout, (float*)Pout, c->flags, c->tile_entries,
-              c->tile_off, c->tile_nown, c->g, ntx, (int)c->n_tiles, kphys<float>(c->ph), c->small + 4);
+              c->tile_work, c->n_work, c->g, ntx, kphys<float>(c->ph), c->small + 4);
         });
         if (ls) return fail(c, ls, "k_tile_tma launch rejected");
         if (s) return s;
@@ -320,7 +321,7 @@ lbm_status step_fused(lbm_ctx* c, int nsteps) {
     if (c->n_tiles > 0) {
       s = launch(c, LBM_KC_FUSED, "k_tile", [&] {
         ls = launch_tiled<T>(c->g, c->ph, fin, fout, Pin, Pin, nullptr, nullptr, Pout, c->flags, c->tile_entries, c->tile_off,
-                             c->tile_nown, &c->tile_smem_set, c->stream);
+                             c->tile_cnt, &c->tile_smem_set, c->stream);
       });
     } else {
       s = launch(c, LBM_KC_FUSED, "k_march", [&] {
@@ -372,7 +373,7 @@ lbm_status step_tiled16(lbm_ctx* c, int nsteps) {
     s = launch(c, LBM_KC_FUSED, "k_tile", [&] {
       ls = launch_tiled<T>(c->g, c->ph, fin, fout, P, Pref, c->Ubuf[c->cur], c->Ubuf[c->cur ^ 1], Po, c->flags,
                            c->tile_entries, c->tile_off,
-                           c->tile_nown, &c->tile_smem_set, c->stream);
+                           c->tile_cnt, &c->tile_smem_set, c->stream);
     });
     if (ls) return fail(c, ls, "tiled kernel launch rejected");
     if (s) return s;
@@ -554,7 +555,8 @@ lbm_status lbm_create(const lbm_params* params, void* d_workspace, size_t bytes,
   c->tma = uses_tma(params);
   c->tile_entries = c->n_tiles ? (uint16_t*)(c->ws + L.tent) : nullptr;
   c->tile_off = c->n_tiles ? (int*)(c->ws + L.toff) : nullptr;
-  c->tile_nown = c->n_tiles ? (int*)(c->ws + L.tnown) : nullptr;
+  c->tile_cnt = c->n_tiles ? (int2*)(c->ws + L.tcnt) : nullptr;
+  c->tile_work = c->n_tiles && uses_tma(params) ? (int4*)(c->ws + L.twork) : nullptr;
   c->n_halo_tiles = uses_halo(params) ? halo_tile_count(g) : 0;
   c->halo_entries = c->n_halo_tiles ? (uint16_t*)(c->ws + L.hent) : nullptr;
   c->halo_off = c->n_halo_tiles ? (int*)(c->ws + L.hoff) : nullptr;
@@ -648,13 +650,24 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* d_mask) {
     // scan, total at tile_off[n_tiles]), entries
     const int ntx = (g.nx + TILE_W - 1) / TILE_W;
     const int nt = (int)c->n_tiles;
-    k_tile_lists<<<nt, TILE_LIST_THREADS, 0, c->stream>>>(c->flags, g, ntx, nullptr, c->tile_off, c->tile_nown, nullptr);
+    k_tile_lists<<<nt, TILE_LIST_THREADS, 0, c->stream>>>(c->flags, g, ntx, nullptr, c->tile_off, c->tile_cnt, nullptr);
     if ((s = after_launch(c, "k_tile_lists(count)"))) return s;
     k_iface_scan<<<1, 1024, 0, c->stream>>>(c->tile_off, nt, c->tile_off + nt);
     if ((s = after_launch(c, "k_iface_scan(tiles)"))) return s;
     k_tile_lists<<<nt, TILE_LIST_THREADS, 0, c->stream>>>(c->flags, g, ntx, c->tile_off, nullptr, nullptr,
                                                      c->tile_entries);
     if ((s = after_launch(c, "k_tile_lists(write)"))) return s;
+    if (c->tile_work) {
+      // the TMA schedule's work list: the tiles with owned nodes, in order
+      k_tile_work<<<1, 1024, 0, c->stream>>>(c->tile_cnt, c->tile_off, nt, c->tile_work, c->small + 5);
+      if ((s = after_launch(c, "k_tile_work"))) return s;
+      int nw = 0;
+      s = check_cuda(c, cudaMemcpyAsync(&nw, c->small + 5, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                     "cudaMemcpyAsync");
+      if (!s) s = check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+      if (s) return s;
+      c->n_work = nw;
+    }
   }
   if (c->n_halo_tiles > 0) {
     // per-tile lists of the halo schedule: counts and fluid bitmasks,

@@ -27,7 +27,7 @@ struct BatchDesc {
   const uint16_t* flags;
   const uint16_t* tile_entries;  // tiled schedule: the member's per-tile lists
   const int* tile_off;
-  const int* tile_nown;
+  const int2* tile_cnt;
   int n_tiles, ntx;
   const int* fluid_list;
   const int* iface_list;
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MINB)
   const int cur = D.cur ^ parity, pcur = D.pcur ^ parity;
   tile_step<T>(b.y, D.n_tiles, (const T*)D.f[cur], (T*)D.f[cur ^ 1], (const C*)D.Pbuf[pcur],
                (const C*)D.Pbuf[pcur], nullptr, nullptr, (C*)D.Pbuf[pcur ^ 1], D.flags, D.tile_entries,
-               D.tile_off, D.tile_nown, D.g, D.ntx, D.ph);
+               D.tile_off, D.tile_cnt, D.g, D.ntx, D.ph);
 }
 
 template <typename T>
@@ -211,7 +211,7 @@ void fill_descs(lbm_batch* b) {
     d.flags = c->flags;
     d.tile_entries = c->tile_entries;
     d.tile_off = c->tile_off;
-    d.tile_nown = c->tile_nown;
+    d.tile_cnt = c->tile_cnt;
     d.n_tiles = (int)c->n_tiles;
     d.ntx = (c->g.nx + TILE_W - 1) / TILE_W;
     d.fluid_list = c->fluid_list;

@@ -48,7 +48,10 @@ struct lbm_ctx {
   int* fluid_list;     // fluid nodes in node order, edge nodes tagged (padded indices)
   uint16_t* tile_entries; // tiled schedule: per-tile lists of region slots (null if unused)
   int* tile_off;       // tiled schedule: first entry of each tile, total at [ntiles]
-  int* tile_nown;      // tiled schedule: owned fluid nodes of each tile
+  int2* tile_cnt;      // tiled schedule: (owned fluid nodes, listed fluid nodes) of each tile
+  int4* tile_work;     // TMA schedule: the tiles with owned nodes, in order: (tile, first entry,
+                       // listed nodes, owned nodes); their number at small[5]
+  int n_work;          // entries of tile_work (read back by lbm_set_geometry)
   int64_t n_tiles;
   bool tile_smem_set;  // k_tile's dynamic shared memory limit raised on this context's device
   uint16_t* halo_entries; // halo schedule: per-tile lists of region slots (null if unused)

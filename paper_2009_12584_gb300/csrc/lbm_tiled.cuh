@@ -63,13 +63,15 @@ inline int64_t tile_count(const Geo& g) {
 }
 
 // Per-tile lists, two passes over the same deterministic order. Count pass
-// (entries == nullptr): counts[tile] = fluid nodes of the region, nown[tile]
-// = fluid nodes owned by the tile. Write pass: entries from offsets[tile]
-// on, the owned nodes first.
+// (entries == nullptr): counts[tile] = fluid nodes of the region rounded up
+// to a multiple of 8 (so that every tile's list starts on a 16-byte
+// boundary after the scan, for bulk copies), cnt[tile] = (fluid nodes owned
+// by the tile, fluid nodes of the region). Write pass: entries from
+// offsets[tile] on, the owned nodes first.
 static __global__ void __launch_bounds__(TILE_LIST_THREADS) k_tile_lists(const uint16_t* __restrict__ flags, Geo g,
                                                                     int ntx, const int* __restrict__ offsets,
                                                                     int* __restrict__ counts,
-                                                                    int* __restrict__ nown,
+                                                                    int2* __restrict__ cnt,
                                                                     uint16_t* __restrict__ entries) {
   __shared__ int warp_cnt[TILE_LIST_THREADS / 32];
   const int tile = blockIdx.x;
@@ -109,8 +111,8 @@ static __global__ void __launch_bounds__(TILE_LIST_THREADS) k_tile_lists(const u
     if (round == 0) n_own = base;
   }
   if (!entries && threadIdx.x == 0) {
-    counts[tile] = base;
-    nown[tile] = n_own;
+    counts[tile] = (base + 7) & ~7;
+    cnt[tile] = make_int2(n_own, base);
   }
 }
 
@@ -131,15 +133,16 @@ __device__ __forceinline__ void tile_step(int tile, int n_tiles, const T* __rest
                                           const UPair* __restrict__ Uref, UPair* __restrict__ Uo,
                                           typename Pop<T>::C* __restrict__ Po, const uint16_t* __restrict__ flags,
                                           const uint16_t* __restrict__ entries, const int* __restrict__ offsets,
-                                          const int* __restrict__ nown, const Geo& g, int ntx,
+                                          const int2* __restrict__ cnt, const Geo& g, int ntx,
                                           const PhysK<typename Pop<T>::C>& ph) {
   using C = typename Pop<T>::C;
   using V = typename CPair<C>::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* s = reinterpret_cast<V*>(smem_raw);
-  const int n_own = nown[tile];
+  const int2 cn = cnt[tile];
+  const int n_own = cn.x;
   if (n_own == 0) return;  // the whole CTA: nothing owned, nothing to store
-  const int e0 = offsets[tile], n_all = offsets[tile + 1] - e0;
+  const int e0 = offsets[tile], n_all = cn.y;
   // The entries are the first load of every node and its pulls depend on
   // them: ask L2 for the entries of the tile TILE_AHEAD launches later (one
   // 128-byte line per 64 entries, enough lines for a full region).
@@ -248,9 +251,9 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MINB)
            const typename Pop<T>::C* __restrict__ Pref, const UPair* __restrict__ Uref,
            UPair* __restrict__ Uo, typename Pop<T>::C* __restrict__ Po,
            const uint16_t* __restrict__ flags,
-           const uint16_t* __restrict__ entries, const int* __restrict__ offsets, const int* __restrict__ nown,
+           const uint16_t* __restrict__ entries, const int* __restrict__ offsets, const int2* __restrict__ cnt,
            Geo g, int ntx, PhysK<typename Pop<T>::C> ph) {
-  tile_step<T>(blockIdx.x, gridDim.x, f, fo, P, Pref, Uref, Uo, Po, flags, entries, offsets, nown, g, ntx, ph);
+  tile_step<T>(blockIdx.x, gridDim.x, f, fo, P, Pref, Uref, Uo, Po, flags, entries, offsets, cnt, g, ntx, ph);
 }
 
 template <typename T>
@@ -264,7 +267,7 @@ template <typename T>
 inline lbm_status launch_tiled(const Geo& g, const Phys& ph, const T* fin, T* fout, const typename Pop<T>::C* P,
                                const typename Pop<T>::C* Pref, const UPair* Uref, UPair* Uo,
                                typename Pop<T>::C* Po, const uint16_t* flags,
-                               const uint16_t* entries, const int* offsets, const int* nown, bool* smem_set,
+                               const uint16_t* entries, const int* offsets, const int2* cnt, bool* smem_set,
                                cudaStream_t stream) {
   constexpr size_t SMEM = tile_smem<T>();
   auto kern = k_tile<T>;
@@ -275,7 +278,7 @@ inline lbm_status launch_tiled(const Geo& g, const Phys& ph, const T* fin, T* fo
   }
   const int ntx = (g.nx + TILE_W - 1) / TILE_W;
   const int64_t nt = tile_count(g);
-  kern<<<(unsigned)nt, TILE_THREADS, SMEM, stream>>>(fin, fout, P, Pref, Uref, Uo, Po, flags, entries, offsets, nown, g, ntx,
+  kern<<<(unsigned)nt, TILE_THREADS, SMEM, stream>>>(fin, fout, P, Pref, Uref, Uo, Po, flags, entries, offsets, cnt, g, ntx,
                                                      kphys<typename Pop<T>::C>(ph));
   return LBM_OK;
 }

@@ -2,17 +2,20 @@
 // Accelerator (TMA): FP32 storage, the same per-tile lists, node arithmetic
 // and results (bit for bit) as k_tile.
 //
-// k_tile pulls every population of every listed node with its own load
-// and waits for them (list entry -> pulls -> update is a chain of dependent
-// global round trips per node). Here a persistent CTA (one per SM) walks its
-// tiles (blockIdx.x, + gridDim.x, ...) and, while it updates one tile, one
-// thread has the TMA copy the next tile's inputs into the other half of a
-// double buffer: the nine population planes and the density plane over the
-// (TILE_W + 4) x (TILE_H + 4) window that the tile and its one-node ring
-// pull from (ten 2-D boxes, no per-node address arithmetic, no registers
-// held by loads in flight). An mbarrier per buffer counts the bytes in; the
-// wait on it is bounded (see TMA_SPIN_LIMIT). Stores, the ring, phase 2
-// and the periodic images are those of k_tile.
+// k_tile pulls every population of every listed node with its own load and
+// waits for them (list entry -> pulls -> update is a chain of dependent
+// global round trips per node). Here a persistent CTA (one per SM) walks a
+// work list of the tiles that own fluid nodes (items blockIdx.x,
+// + gridDim.x, ...) and, while it updates one tile, the TMA copies the next
+// two tiles' inputs into the other two thirds of a triple buffer: the nine
+// population planes and the density plane over the (TILE_W + 4) x
+// (TILE_H + 4) window that the tile and its one-node ring pull from (ten
+// 2-D boxes) and the tile's list entries (one 1-D bulk copy; the lists are
+// padded to 16-byte boundaries). No per-node address arithmetic, no
+// registers held by loads in flight, no dependent global load before a
+// tile's update. An mbarrier per buffer counts the bytes in; the wait on it
+// is bounded (TMA_SPIN_LIMIT). Stores, the ring, phase 2 and the periodic
+// images are those of k_tile.
 #pragma once
 
 #include <cuda.h>  // CUtensorMap
@@ -26,7 +29,10 @@ constexpr int TMA_WH = TILE_H + 4;                  // window rows
 constexpr int TMA_BOX_X = 2 * TMA_WW;               // floats per window row (component pairs)
 constexpr int TMA_PLANE_BYTES = TMA_BOX_X * TMA_WH * 4;
 constexpr int TMA_SLOT_BYTES = (TMA_PLANE_BYTES + 127) / 128 * 128;  // 128-byte aligned destinations
-constexpr int TMA_BUF_BYTES = 10 * TMA_SLOT_BYTES;  // nine population planes and the density plane
+constexpr int TMA_ENTRY_BYTES = (TILE_RS + 7) / 8 * 16;  // a tile's list, padded to 8 entries
+constexpr int TMA_NBUF = 3;
+// nine population planes, the density plane and the entries, 128-byte aligned
+constexpr int TMA_BUF_BYTES = (10 * TMA_SLOT_BYTES + TMA_ENTRY_BYTES + 127) / 128 * 128;
 #ifndef LBM_TMA_THREADS
 #define LBM_TMA_THREADS 512
 #endif
@@ -40,7 +46,7 @@ static_assert(TILE_W % 2 == 0, "window x starts must be 16-byte aligned: 4 * 2 *
 
 template <typename T>
 constexpr size_t tma_smem() {
-  return 2 * (size_t)TMA_BUF_BYTES + (size_t)9 * TILE_RS * sizeof(float2) + 128;
+  return TMA_NBUF * (size_t)TMA_BUF_BYTES + (size_t)9 * TILE_RS * sizeof(float2) + 128;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -89,29 +95,66 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// The next tile this CTA owns after tile `from` (stride gridDim.x) that has
-// nodes of its own, or -1.
-__device__ __forceinline__ int next_tile(const int* __restrict__ nown, int from, int n_tiles) {
-  for (int t = from; t < n_tiles; t += gridDim.x)
-    if (__ldg(nown + t) > 0) return t;
-  return -1;
+// A contiguous 16-byte-aligned run of global memory into shared memory,
+// counted on bar (bytes: a multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 
-// Issue the ten copies of tile `tile`'s window into buffer `buf` (one thread).
+// The TMA schedule's work list: the tiles with owned nodes in tile order,
+// as (tile, first entry, listed nodes, owned nodes), and their number in
+// *n_work. One CTA of 1024 threads, fixed-order scan (deterministic).
+static __global__ void __launch_bounds__(1024)
+    k_tile_work(const int2* __restrict__ cnt, const int* __restrict__ offsets, int n_tiles, int4* __restrict__ work,
+                int* __restrict__ n_work) {
+  __shared__ int warp_sums[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < n_tiles; base += 1024) {
+    const int t = base + threadIdx.x;
+    const int2 c = t < n_tiles ? cnt[t] : make_int2(0, 0);
+    const bool keep = c.x > 0;
+    const unsigned ball = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) warp_sums[wid] = __popc(ball);
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int w = 0; w < 32; ++w) {
+      before += w < wid ? warp_sums[w] : 0;
+      all += warp_sums[w];
+    }
+    if (keep) work[carry + before + __popc(ball & ((1u << lane) - 1u))] = make_int4(t, offsets[t], c.y, c.x);
+    __syncthreads();
+    if (threadIdx.x == 0) carry += all;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *n_work = carry;
+}
+
+// Issue the copies of work item w (tile's window and entries) into buffer
+// `buf` (one thread).
 __device__ __forceinline__ void tma_issue(unsigned char* buf, uint64_t* bar, const CUtensorMap* mapf,
-                                          const CUtensorMap* mapP, int tile, int ntx) {
+                                          const CUtensorMap* mapP, const uint16_t* __restrict__ entries, int4 w,
+                                          int ntx) {
+  const int tile = w.x;
   const int x0 = (tile % ntx) * TILE_W, y0 = (tile / ntx) * TILE_H;
   // padded coordinates of the window's first pair: column x0 - 2 + LP (its
   // first float, times 4 bytes, is 16-byte aligned: TILE_W is even), row
   // y0 - 2 + GH
   const int xf = 2 * (x0 - 2 + LP), yw = y0 - 2 + GH;
-  // order the generic-proxy reads of this buffer (the previous tile) before
+  const uint32_t ebytes = (uint32_t)((w.z + 7) & ~7) * 2;  // the list, padded to 16 bytes
+  // order the generic-proxy reads of this buffer (three tiles back) before
   // the copies' writes
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  mbar_expect_tx(bar, 10u * TMA_PLANE_BYTES);
+  mbar_expect_tx(bar, 10u * TMA_PLANE_BYTES + ebytes);
 #pragma unroll
   for (int i = 0; i < 9; ++i) tma_load_3d(buf + i * TMA_SLOT_BYTES, mapf, xf, yw, i, bar);
   tma_load_2d(buf + 9 * TMA_SLOT_BYTES, mapP, xf, yw, bar);
+  bulk_load(buf + 10 * TMA_SLOT_BYTES, entries + w.y, ebytes, bar);
 }
 
 // err: set to 1 when a copy was not seen to complete within the bound (the
@@ -119,62 +162,63 @@ __device__ __forceinline__ void tma_issue(unsigned char* buf, uint64_t* bar, con
 static __global__ void __launch_bounds__(TMA_THREADS, 1)
     k_tile_tma(const __grid_constant__ CUtensorMap mapf, const __grid_constant__ CUtensorMap mapP,
                float* __restrict__ fo, float* __restrict__ Po, const uint16_t* __restrict__ flags,
-               const uint16_t* __restrict__ entries, const int* __restrict__ offsets, const int* __restrict__ nown,
-               Geo g, int ntx, int n_tiles, PhysK<float> ph, int* __restrict__ err) {
+               const uint16_t* __restrict__ entries, const int4* __restrict__ work, int n_work, Geo g, int ntx,
+               PhysK<float> ph, int* __restrict__ err) {
   using V = float2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  unsigned char* buf[2] = {base, base + TMA_BUF_BYTES};
-  V* s = reinterpret_cast<V*>(base + 2 * TMA_BUF_BYTES);  // f*(t+1) of the region, [9][TILE_RS]
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int tile_of[2];
+  V* s = reinterpret_cast<V*>(base + TMA_NBUF * TMA_BUF_BYTES);  // f*(t+1) of the region, [9][TILE_RS]
+  __shared__ __align__(8) uint64_t bar[TMA_NBUF];
   const float zr[2][9] = {};  // storage references: zero for 4-byte populations
+  const int G = gridDim.x;
+  int4 wnext = make_int4(-1, 0, 0, 0);  // thread 0: the item two ahead of the current one
   if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int b = 0; b < TMA_NBUF; ++b) mbar_init(&bar[b], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    const int t0 = next_tile(nown, blockIdx.x, n_tiles);
-    tile_of[0] = t0;
-    if (t0 >= 0) tma_issue(buf[0], &bar[0], &mapf, &mapP, t0, ntx);
+    for (int k = 0; k < TMA_NBUF - 1; ++k) {
+      const int wk = blockIdx.x + k * G;
+      if (wk < n_work) tma_issue(base + k * TMA_BUF_BYTES, &bar[k], &mapf, &mapP, entries, __ldg(work + wk), ntx);
+    }
+    const int w2 = blockIdx.x + (TMA_NBUF - 1) * G;
+    if (w2 < n_work) wnext = __ldg(work + w2);
   }
   __syncthreads();
-  uint32_t parity[2] = {0, 0};
   for (int n = 0;; ++n) {
-    const int cur = n & 1;
-    const int tile = tile_of[cur];
-    if (tile < 0) break;
+    const int wn = blockIdx.x + n * G;
+    if (wn >= n_work) break;
+    const int cur = n % TMA_NBUF;
+    unsigned char* buf = base + cur * TMA_BUF_BYTES;
     if (threadIdx.x == 0) {
-      // the next tile's window into the other buffer, freed by the barrier
-      // that ended the previous iteration; its list entries towards L2
-      const int t1 = next_tile(nown, tile + gridDim.x, n_tiles);
-      tile_of[cur ^ 1] = t1;
-      if (t1 >= 0) {
-        tma_issue(buf[cur ^ 1], &bar[cur ^ 1], &mapf, &mapP, t1, ntx);
-        const int e1 = __ldg(offsets + t1), n1 = __ldg(offsets + t1 + 1) - e1;
-        for (int l = 0; l < n1; l += 64) asm volatile("prefetch.global.L2 [%0];" ::"l"(entries + e1 + l));
+      // the item TMA_NBUF - 1 ahead into the buffer the previous iteration
+      // freed (its closing barrier), then the item after it towards a register
+      const int wa = wn + (TMA_NBUF - 1) * G;
+      if (wa < n_work) {
+        const int ba = (n + TMA_NBUF - 1) % TMA_NBUF;
+        tma_issue(base + ba * TMA_BUF_BYTES, &bar[ba], &mapf, &mapP, entries, wnext, ntx);
+        if (wa + G < n_work) wnext = __ldg(work + wa + G);
       }
     }
-    const bool ok = mbar_wait(&bar[cur], parity[cur]);
+    const int4 item = __ldg(work + wn);  // (tile, first entry, listed nodes, owned nodes)
+    const bool ok = mbar_wait(&bar[cur], (uint32_t)((n / TMA_NBUF) & 1));
     if (__syncthreads_or(!ok)) {
       // a copy did not complete within the bound: report it and stop this
       // CTA after waiting (bounded) for the copies it has in flight
       if (threadIdx.x == 0) {
         atomicExch(err, 1);
-        mbar_wait(&bar[cur], parity[cur]);
-        if (tile_of[cur ^ 1] >= 0) mbar_wait(&bar[cur ^ 1], parity[cur ^ 1]);
+        for (int k = n; k < n + TMA_NBUF; ++k)
+          if (blockIdx.x + k * G < n_work) mbar_wait(&bar[k % TMA_NBUF], (uint32_t)((k / TMA_NBUF) & 1));
       }
       break;
     }
-    parity[cur] ^= 1;
-    const float* win = reinterpret_cast<const float*>(buf[cur]);
-    const int n_own = nown[tile];
-    const int e0 = offsets[tile], n_all = offsets[tile + 1] - e0;
+    const float* win = reinterpret_cast<const float*>(buf);
+    const uint16_t* ent = reinterpret_cast<const uint16_t*>(buf + 10 * TMA_SLOT_BYTES);
+    const int tile = item.x, n_all = item.z, n_own = item.w;
     const int x0 = (tile % ntx) * TILE_W, y0 = (tile / ntx) * TILE_H;
     const int korg = g.idx(x0 - 1, y0 - 1);  // padded index of region slot 0
     for (int b = 0; b < n_all; b += TMA_THREADS) {
       const int t = b + threadIdx.x;
       const bool valid = t < n_all;
-      const uint16_t e = valid ? __ldg(entries + e0 + t) : uint16_t(0);
+      const uint16_t e = valid ? ent[t] : uint16_t(0);
       const bool warp_edge = __any_sync(0xffffffffu, (e & TE_SOLIDNB) != 0);
       const bool warp_border = __any_sync(0xffffffffu, (e & TE_BORDER) != 0);
       if (!valid) continue;
@@ -218,7 +262,7 @@ static __global__ void __launch_bounds__(TMA_THREADS, 1)
     }
     __syncthreads();
     for (int t = threadIdx.x; t < n_own; t += TMA_THREADS) {
-      const uint16_t e = __ldg(entries + e0 + t);
+      const uint16_t e = ent[t];
       const int slot = e & TE_SLOT;
       const int row = slot / TILE_RW, col = slot - row * TILE_RW;
       const int k = korg + row * g.px + col;

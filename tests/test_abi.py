@@ -109,18 +109,23 @@ def test_argument_checks_before_any_cuda_call(lib):
 
 def test_tiled_schedule_workspace_without_gpu():
     """The tiled schedule adds its per-tile lists (2 bytes per region slot of
-    each 32 x 14 tile plus per-tile offsets and counts, each array 256-byte
-    aligned), and for 16-bit storage a third density plane pair; AUTO keeps
-    them for 4- and 8-byte storage only; an unknown schedule is rejected."""
+    each 32 x 14 tile plus per-tile offsets and (owned, listed) count pairs,
+    each array 256-byte aligned), and for 16-bit storage a third density
+    plane pair; the TMA schedule (FP32 only) adds a 16-byte work item per
+    tile; AUTO keeps the tiled lists for 4- and 8-byte storage only; an
+    unknown schedule is rejected."""
     lbm.load()
     align = lambda n: (n + 255) // 256 * 256
     for nx, ny in ((8192, 8192), (100, 70), (4, 4)):
         nt = -(-nx // 32) * -(-ny // 14)
-        extra = align(nt * 34 * 16 * 2) + align((nt + 1) * 4) + align(nt * 4)
+        extra = align(nt * 34 * 16 * 2) + align((nt + 1) * 4) + align(nt * 8)
         for st in ("fp32", "fp64"):
             base = lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="two_pass"))
             tiled = lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="tiled"))
             assert tiled - base == extra, (nx, ny, st)
+            if st == "fp32":
+                tma = lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="tma"))
+                assert tma - tiled == align(nt * 16), (nx, ny)
             # AUTO runs the tiled schedule for 4- and 8-byte storage
             assert lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="auto")) == tiled
         px = -(-(32 + nx + 4) // 32) * 32  # padded pitch and rows
