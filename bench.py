@@ -367,9 +367,25 @@ def run_batched(storage, steps, warmup, nsims=512, l2_fetch=128):
     e1.record(stream)
     torch.cuda.synchronize()
     t_ms = e0.elapsed_time(e1)
+    launches = b.launch_count - l0
+    sched = b.config()[0]
+    # the schedule the autotuner did not keep, timed the same way after the
+    # measured steps (for the record; it does not enter the value)
+    others = {}
+    for other in ("two_pass", "tiled"):
+        if other == sched or (other == "tiled" and storage not in ("fp32", "fp64")):
+            continue
+        b.set_schedule(other)
+        b.step(2)
+        e0.record(stream)
+        b.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        others[other] = round(nf * steps / (e0.elapsed_time(e1) / 1e3) / 1e6, 1)
     out = {"value": round(nf * steps / (t_ms / 1e3) / 1e6, 1), "unit": "MLUPS", "ms_per_step": round(t_ms / steps, 4),
-           "sims": nsims, "fluid_nodes": nf, "threads_per_block": choice[0], "steps_per_graph": choice[1],
-           "gpu_launches": b.launch_count - l0, "setup_s": round(setup, 1),
+           "sims": nsims, "fluid_nodes": nf, "schedule": sched, "threads_per_block": choice[0],
+           "steps_per_graph": choice[1], "other_schedules_mlups": others,
+           "gpu_launches": launches, "setup_s": round(setup, 1),
            "workload": "512 inclined-wall simulations, 64x64..512x256, beta U[0,45], theta U[45,135], "
                        "MC/LLKC/improved mixed, seed 0", "l2_fetch_granularity_bytes": l2_fetch}
     b.close()

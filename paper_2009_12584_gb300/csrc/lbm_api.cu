@@ -239,9 +239,12 @@ lbm_status step_two_pass(lbm_ctx* c, int nsteps) {
     T* fout = (T*)c->f[c->cur ^ 1];
     C* P = (C*)c->Pbuf[c->pcur ^ 1];
     const C* Pref = (const C*)c->Pbuf[c->pcur];
+    // velocity references (16-bit storage only) run their own instantiations
+    const bool vr = kDev<T> && c->prm.velocity_refs;
     lbm_status s = launch(c, LBM_KC_DENSITY, "k_density_list", [&] {
-      k_density_list<T><<<nb, 256, 0, c->stream>>>(fin, P, Pref, c->Ubuf[c->cur], c->flags, c->fluid_list, c->n_fluid, c->g,
-                                                  kphys<C>(c->ph));
+      auto kd = vr ? k_density_list<T, kDev<T>> : k_density_list<T, false>;
+      kd<<<nb, 256, 0, c->stream>>>(fin, P, Pref, c->Ubuf[c->cur], c->flags, c->fluid_list, c->n_fluid, c->g,
+                                    kphys<C>(c->ph));
     });
     if (s) return s;
     if (c->ph.bc == BC_VAVG && c->n_iface > 0) {
@@ -252,9 +255,9 @@ lbm_status step_two_pass(lbm_ctx* c, int nsteps) {
       if (s) return s;
     }
     s = launch(c, LBM_KC_COLLIDE, "k_collide_list", [&] {
-      k_collide_list<T><<<nbc, COLLIDE_THREADS, 0, c->stream>>>(fin, fout, P, Pref, c->Ubuf[c->cur],
-                                                                c->Ubuf[c->cur ^ 1], c->flags, c->fluid_list,
-                                                                c->n_fluid, c->g, kphys<C>(c->ph));
+      auto kc = vr ? k_collide_list<T, kDev<T>> : k_collide_list<T, false>;
+      kc<<<nbc, COLLIDE_THREADS, 0, c->stream>>>(fin, fout, P, Pref, c->Ubuf[c->cur], c->Ubuf[c->cur ^ 1], c->flags,
+                                                 c->fluid_list, c->n_fluid, c->g, kphys<C>(c->ph));
     });
     if (s) return s;
     c->cur ^= 1;

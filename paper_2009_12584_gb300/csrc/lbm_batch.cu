@@ -41,7 +41,10 @@ struct BatchDesc {
 // Densities of the members' current populations. into: 1 into Pbuf[pcur ^ 1]
 // (two-pass: the plane the collide pass reads), 0 into Pbuf[pcur] (tiled:
 // rho(t) before the first tiled step; 4- and 8-byte storage).
-template <typename T>
+// VR: whether members' velocity planes may be read (16-bit storage with
+// velocity references in at least one member; a member without them has
+// null planes). Without it the kernels carry no code for them.
+template <typename T, bool VR = false>
 __global__ void __launch_bounds__(256) k_density_batch(const BatchDesc<typename Pop<T>::C>* __restrict__ d,
                                                        const int2* __restrict__ blk, int parity, int into) {
   using C = typename Pop<T>::C;
@@ -50,7 +53,8 @@ __global__ void __launch_bounds__(256) k_density_batch(const BatchDesc<typename 
   const int cur = D.cur ^ parity, pcur = D.pcur ^ parity;
   const int t = b.y + threadIdx.x;
   if (t < D.n_fluid)
-    density_node<T>((const T*)D.f[cur], (C*)D.Pbuf[pcur ^ into], (const C*)D.Pbuf[pcur], D.Ubuf[cur], D.flags,
+    density_node<T>((const T*)D.f[cur], (C*)D.Pbuf[pcur ^ into], (const C*)D.Pbuf[pcur], VR ? D.Ubuf[cur] : nullptr,
+                    D.flags,
                     D.fluid_list, t, D.g);
 }
 
@@ -79,7 +83,7 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MINB)
                D.tile_off, D.tile_cnt, D.g, D.ntx, D.ph);
 }
 
-template <typename T>
+template <typename T, bool VR = false>
 __global__ void __launch_bounds__(256, 4) k_collide_batch(const BatchDesc<typename Pop<T>::C>* __restrict__ d,
                                                        const int2* __restrict__ blk, int parity) {
   using C = typename Pop<T>::C;
@@ -87,7 +91,8 @@ __global__ void __launch_bounds__(256, 4) k_collide_batch(const BatchDesc<typena
   const BatchDesc<C>& D = d[b.x];
   const int cur = D.cur ^ parity, pcur = D.pcur ^ parity;
   collide_node<T>((const T*)D.f[cur], (T*)D.f[cur ^ 1], (const C*)D.Pbuf[pcur ^ 1], (const C*)D.Pbuf[pcur],
-                  D.Ubuf[cur], D.Ubuf[cur ^ 1], D.flags, D.fluid_list, b.y + threadIdx.x, D.n_fluid, D.g, D.ph);
+                  VR ? D.Ubuf[cur] : nullptr, VR ? D.Ubuf[cur ^ 1] : nullptr, D.flags, D.fluid_list, b.y + threadIdx.x,
+                  D.n_fluid, D.g, D.ph);
 }
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -118,6 +123,7 @@ struct lbm_batch {
   int n_fblk, n_iblk, n_tblk;
   int schedule;         // LBM_KERNEL_TWO_PASS or LBM_KERNEL_TILED
   bool tiled_ok;        // 4- or 8-byte storage and every member keeps tile lists
+  bool vr;              // 16-bit storage and some member keeps velocity references
   int bs;               // threads per block of the density and collide kernels
   void* h_desc;         // host staging of the descriptors
   int2* h_tab;          // host staging of the block tables
@@ -244,8 +250,10 @@ lbm_status launch_step(lbm_batch* b, int p) {
     }
     return bcuda(b, cudaGetLastError(), "batched tiled step launch");
   }
+  const bool vr = kDev<T> && b->vr;
   if (b->n_fblk > 0) {
-    k_density_batch<T><<<b->n_fblk, b->bs, 0, b->stream>>>(d, b->d_fblk, p, 1);
+    auto kd = vr ? k_density_batch<T, kDev<T>> : k_density_batch<T, false>;
+    kd<<<b->n_fblk, b->bs, 0, b->stream>>>(d, b->d_fblk, p, 1);
     b->launches++;
   }
   if (b->n_iblk > 0) {
@@ -253,7 +261,8 @@ lbm_status launch_step(lbm_batch* b, int p) {
     b->launches++;
   }
   if (b->n_fblk > 0) {
-    k_collide_batch<T><<<b->n_fblk, b->bs, 0, b->stream>>>(d, b->d_fblk, p);
+    auto kc = vr ? k_collide_batch<T, kDev<T>> : k_collide_batch<T, false>;
+    kc<<<b->n_fblk, b->bs, 0, b->stream>>>(d, b->d_fblk, p);
     b->launches++;
   }
   return bcuda(b, cudaGetLastError(), "batched step launch");
@@ -290,8 +299,10 @@ lbm_status build_graph(lbm_batch* b, int steps) {
     int p = k & 1;
     int into = tiled ? 0 : 1;
     const int2* tabs[3] = {b->d_fblk, b->d_iblk, tiled ? b->d_tblk : b->d_fblk};
-    void* fns[3] = {(void*)k_density_batch<T>, (void*)k_virtual_batch<C>,
-                    tiled ? tile_fn : (void*)k_collide_batch<T>};
+    const bool vr = kDev<T> && b->vr;
+    void* fns[3] = {vr ? (void*)k_density_batch<T, kDev<T>> : (void*)k_density_batch<T, false>,
+                    (void*)k_virtual_batch<C>,
+                    tiled ? tile_fn : vr ? (void*)k_collide_batch<T, kDev<T>> : (void*)k_collide_batch<T, false>};
     const int grids[3] = {tiled ? 0 : b->n_fblk, b->n_iblk, tiled ? b->n_tblk : b->n_fblk};
     const int blocks[3] = {b->bs, 128, tiled ? TILE_THREADS : b->bs};
     const size_t smem[3] = {0, 0, tiled ? tile_smem<T>() : 0};
@@ -412,6 +423,8 @@ lbm_status lbm_batch_create(int32_t n, lbm_ctx* const* ctxs, void* d_workspace, 
   b->d_fblk = (int2*)(b->ws + L.fblk);
   b->d_iblk = (int2*)(b->ws + L.iblk);
   b->tiled_ok = batch_tiled_ok(n, ctxs);
+  b->vr = false;
+  for (int i = 0; i < n; ++i) b->vr = b->vr || ctxs[i]->Ubuf[0] != nullptr;
   b->d_tblk = b->tiled_ok ? (int2*)(b->ws + L.tblk) : nullptr;
   b->schedule = LBM_KERNEL_TWO_PASS;
   b->ctx = (lbm_ctx**)malloc(sizeof(lbm_ctx*) * n);

@@ -171,6 +171,10 @@ struct Pop<double> {
 // small deviations left by the references stay out of FP16's subnormal range
 // (below 2^-14), where precision would be absolute instead of relative;
 // deviations up to 16 in magnitude fit.
+// The difference from and the sum with the reference are explicitly rounded
+// operations (__fsub_rn, __fadd_rn), which the compiler never fuses with the
+// multiply that formed the reference (w_i rho): every kernel encodes and
+// decodes with the same roundings, whatever it inlined around them.
 constexpr float HALF_SCALE = 4096.0f, HALF_UNSCALE = 1.0f / 4096.0f;
 template <>
 struct Pop<__half> {
@@ -179,9 +183,9 @@ struct Pop<__half> {
     return fmaf(__half2float(p[k]), HALF_UNSCALE, ref);
   }
   static __device__ __forceinline__ void st(__half* p, int64_t k, float v, float ref) {
-    p[k] = __float2half_rn((v - ref) * HALF_SCALE);
+    p[k] = __float2half_rn(__fsub_rn(v, ref) * HALF_SCALE);
   }
-  static __device__ __forceinline__ __half enc(float v, float ref) { return __float2half_rn((v - ref) * HALF_SCALE); }
+  static __device__ __forceinline__ __half enc(float v, float ref) { return __float2half_rn(__fsub_rn(v, ref) * HALF_SCALE); }
   static __device__ __forceinline__ float dec(__half v, float ref) { return fmaf(__half2float(v), HALF_UNSCALE, ref); }
   static __device__ __forceinline__ void ld2(const __half* p, int64_t j, float ra, float rb, float& a, float& b) {
     const __half2 v = __ldg(reinterpret_cast<const __half2*>(p + j));
@@ -189,28 +193,28 @@ struct Pop<__half> {
     b = fmaf(__high2float(v), HALF_UNSCALE, rb);
   }
   static __device__ __forceinline__ void st2(__half* p, int64_t j, float a, float b, float ra, float rb) {
-    *reinterpret_cast<__half2*>(p + j) = __floats2half2_rn((a - ra) * HALF_SCALE, (b - rb) * HALF_SCALE);
+    *reinterpret_cast<__half2*>(p + j) = __floats2half2_rn(__fsub_rn(a, ra) * HALF_SCALE, __fsub_rn(b, rb) * HALF_SCALE);
   }
 };
 template <>
 struct Pop<__nv_bfloat16> {
   using C = float;
   static __device__ __forceinline__ float ld(const __nv_bfloat16* p, int64_t k, float ref) {
-    return __bfloat162float(p[k]) + ref;
+    return __fadd_rn(__bfloat162float(p[k]), ref);
   }
   static __device__ __forceinline__ void st(__nv_bfloat16* p, int64_t k, float v, float ref) {
-    p[k] = __float2bfloat16_rn(v - ref);
+    p[k] = __float2bfloat16_rn(__fsub_rn(v, ref));
   }
-  static __device__ __forceinline__ __nv_bfloat16 enc(float v, float ref) { return __float2bfloat16_rn(v - ref); }
-  static __device__ __forceinline__ float dec(__nv_bfloat16 v, float ref) { return __bfloat162float(v) + ref; }
+  static __device__ __forceinline__ __nv_bfloat16 enc(float v, float ref) { return __float2bfloat16_rn(__fsub_rn(v, ref)); }
+  static __device__ __forceinline__ float dec(__nv_bfloat16 v, float ref) { return __fadd_rn(__bfloat162float(v), ref); }
   static __device__ __forceinline__ void ld2(const __nv_bfloat16* p, int64_t j, float ra, float rb, float& a,
                                              float& b) {
     const __nv_bfloat162 v = __ldg(reinterpret_cast<const __nv_bfloat162*>(p + j));
-    a = __low2float(v) + ra;
-    b = __high2float(v) + rb;
+    a = __fadd_rn(__low2float(v), ra);
+    b = __fadd_rn(__high2float(v), rb);
   }
   static __device__ __forceinline__ void st2(__nv_bfloat16* p, int64_t j, float a, float b, float ra, float rb) {
-    *reinterpret_cast<__nv_bfloat162*>(p + j) = __floats2bfloat162_rn(a - ra, b - rb);
+    *reinterpret_cast<__nv_bfloat162*>(p + j) = __floats2bfloat162_rn(__fsub_rn(a, ra), __fsub_rn(b, rb));
   }
 };
 

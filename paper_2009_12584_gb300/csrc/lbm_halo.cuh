@@ -42,11 +42,14 @@ namespace lbm {
 #ifndef LBM_HALO_H
 #define LBM_HALO_H 14
 #endif
+// 128-thread CTAs, 8 per SM: on the 8192^2 porous medium 2.09 ms per step
+// against 2.34 ms with 256 threads at 4 per SM (improved scheme; Martys-Chen
+// 1.59 against 1.68 ms)
 #ifndef LBM_HALO_THREADS
-#define LBM_HALO_THREADS 256
+#define LBM_HALO_THREADS 128
 #endif
 #ifndef LBM_HALO_MINB
-#define LBM_HALO_MINB 4
+#define LBM_HALO_MINB 8
 #endif
 #ifndef LBM_HALO_AHEAD
 #define LBM_HALO_AHEAD 512

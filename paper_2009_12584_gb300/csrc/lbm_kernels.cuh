@@ -219,15 +219,18 @@ __device__ __forceinline__ void density_node(const T* __restrict__ f, typename P
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_density_list(const T* __restrict__ f, typename Pop<T>::C* __restrict__ P,
+// VR: whether the velocity planes may be read (16-bit storage with velocity
+// references); without it Uref is never touched and the kernel carries no
+// code for it, and 32 registers give 8 CTAs per SM.
+template <typename T, bool VR = false>
+__global__ void __launch_bounds__(256, VR ? 1 : 8) k_density_list(const T* __restrict__ f, typename Pop<T>::C* __restrict__ P,
                                                       const typename Pop<T>::C* __restrict__ Pref,
                                                       const UPair* __restrict__ Uref,
                                                       const uint16_t* __restrict__ flags,
                                                       const int* __restrict__ list, int nfluid, Geo g,
                                                       PhysK<typename Pop<T>::C> ph) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < nfluid) density_node<T>(f, P, Pref, Uref, flags, list, t, g);
+  if (t < nfluid) density_node<T>(f, P, Pref, VR ? Uref : nullptr, flags, list, t, g);
 }
 
 // The update of collide_node for the FP32 compute type, with the two
@@ -368,7 +371,8 @@ __device__ __forceinline__ void collide_node(const T* __restrict__ f, T* __restr
   }
 }
 
-template <typename T>
+// VR as for k_density_list (Uref and Uo untouched without it).
+template <typename T, bool VR = false>
 __global__ void __launch_bounds__(COLLIDE_THREADS, 8) k_collide_list(const T* __restrict__ f, T* __restrict__ fo,
                                                          const typename Pop<T>::C* __restrict__ P,
                                                          const typename Pop<T>::C* __restrict__ Pref,
@@ -378,7 +382,8 @@ __global__ void __launch_bounds__(COLLIDE_THREADS, 8) k_collide_list(const T* __
                                                          const int* __restrict__ list, int nfluid, Geo g,
                                                          PhysK<typename Pop<T>::C> ph) {
   prefetch_list_ahead<COLLIDE_THREADS>(list, nfluid);
-  collide_node<T>(f, fo, P, Pref, Uref, Uo, flags, list, blockIdx.x * blockDim.x + threadIdx.x, nfluid, g, ph);
+  collide_node<T>(f, fo, P, Pref, VR ? Uref : nullptr, VR ? Uo : nullptr, flags, list,
+                  blockIdx.x * blockDim.x + threadIdx.x, nfluid, g, ph);
 }
 
 // ---- K2: virtual solid density of Eq. 8 over the interface-solid list -----

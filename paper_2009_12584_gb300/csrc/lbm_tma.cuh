@@ -14,7 +14,7 @@
 // padded to 16-byte boundaries). No per-node address arithmetic, no
 // registers held by loads in flight, no dependent global load before a
 // tile's update. An mbarrier per buffer counts the bytes in; the wait on it
-// is bounded (TMA_SPIN_LIMIT). Stores, the ring, phase 2 and the periodic
+// is bounded (TMA_WAIT_NS). Stores, the ring, phase 2 and the periodic
 // images are those of k_tile.
 #pragma once
 
@@ -37,9 +37,10 @@ constexpr int TMA_BUF_BYTES = (10 * TMA_SLOT_BYTES + TMA_ENTRY_BYTES + 127) / 12
 #define LBM_TMA_THREADS 512
 #endif
 constexpr int TMA_THREADS = LBM_TMA_THREADS;
-// try_wait rounds before a CTA gives up on a copy and reports it (each round
-// is a hardware-bounded suspend of the waiting thread)
-constexpr unsigned TMA_SPIN_LIMIT = 1u << 24;
+// Nanoseconds (of the global timer) a CTA waits for a tile's copies before
+// it gives up and reports them: far above any copy's latency, short enough
+// to return control to the host within about a second.
+constexpr unsigned long long TMA_WAIT_NS = 1000000000ull;
 static_assert(TMA_BOX_X <= 256 && TMA_WH <= 256, "TMA box dimensions are at most 256");
 static_assert((TMA_BOX_X * 4) % 16 == 0, "the box's inner extent must be a multiple of 16 bytes");
 static_assert(TILE_W % 2 == 0, "window x starts must be 16-byte aligned: 4 * 2 * (x0 - 2 + LP) % 16 == 0");
@@ -62,10 +63,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-// Wait for the phase with the given parity to complete; false after
-// TMA_SPIN_LIMIT rounds.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase with the given parity to complete; false once
+// TMA_WAIT_NS have passed (the timer is read every 256 polls).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (unsigned r = 0; r < TMA_SPIN_LIMIT; ++r) {
+  unsigned long long t0 = 0;
+  for (unsigned long long r = 0;; ++r) {  // 64-bit: never wraps to 0
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -73,8 +81,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((r & 255ull) == 0) {
+      const unsigned long long t = global_ns();
+      if (r == 0)
+        t0 = t;
+      else if (t - t0 > TMA_WAIT_NS)
+        return false;
+    }
   }
-  return false;
 }
 
 // One TMA box of a rank-3 tensor (x, y, plane) into shared memory, counted
