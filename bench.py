@@ -457,7 +457,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
-    ap.add_argument("--kernel", default="auto", choices=["auto", "two_pass", "fused", "tiled"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "two_pass", "fused", "tiled", "halo", "tma"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the fp16/bf16, batched and accuracy arms")
@@ -524,8 +524,9 @@ def main():
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
     pk, pk_kind = peaks()
     # the single-pass class is k_tile under AUTO and TILED (4- and 8-byte
-    # storage), k_march under FUSED
-    tkey = dom if dom != "fused" else ("tile" if effective_schedule(args.kernel, args.storage) == "tiled" else "march")
+    # storage), k_march under FUSED, k_halo under HALO, k_tile_tma under TMA
+    sched = effective_schedule(args.kernel, args.storage)
+    tkey = dom if dom != "fused" else {"tiled": "tile", "fused": "march"}.get(sched, sched)
     traffic = measured_traffic(tkey, args.storage, l2_fetch)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
                 "peak_kind": pk_kind, "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
