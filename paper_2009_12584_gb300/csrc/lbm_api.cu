@@ -328,7 +328,7 @@ lbm_status step_fused(lbm_ctx* c, int nsteps) {
       });
     } else {
       s = launch(c, LBM_KC_FUSED, "k_march", [&] {
-        ls = launch_fused<T>(c->g, c->ph, fin, fout, Pin, Pout, c->flags, c->num_sms, c->stream);
+        ls = launch_fused<T>(c->g, c->ph, fin, fout, Pin, Pout, c->flags, c->num_sms, &c->march_smem_set, c->stream);
       });
     }
     if (ls) return fail(c, ls, "fused kernel launch rejected");

@@ -233,19 +233,17 @@ inline bool fused_supported(const Geo&, const Phys&) {
 }
 
 template <typename T>
+// *smem_set records, per context (one device), that the kernel's dynamic
+// shared memory limit has been raised (FP64 needs 72 KB).
 inline lbm_status launch_fused(const Geo& g, const Phys& ph, const T* fin, T* fout, const typename Pop<T>::C* P,
-                               typename Pop<T>::C* Po, const uint16_t* flags, int num_sms, cudaStream_t stream) {
+                               typename Pop<T>::C* Po, const uint16_t* flags, int num_sms, bool* smem_set,
+                               cudaStream_t stream) {
   using Cfg = MarchCfg<T>;
   auto kern = k_march<T>;
-  if (Cfg::SMEM > 48 * 1024) {
-    static bool configured[64] = {};  // the attribute is set per function and device
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LBM_ERR_CUDA;
-    if (!configured[dev]) {
-      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) != cudaSuccess)
-        return LBM_ERR_CUDA;
-      configured[dev] = true;
-    }
+  if (Cfg::SMEM > 48 * 1024 && !*smem_set) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) != cudaSuccess)
+      return LBM_ERR_CUDA;
+    *smem_set = true;
   }
   const int nstrips = (g.nx + MARCH_OWN - 1) / MARCH_OWN;
   const int gx = (nstrips + MARCH_WARPS - 1) / MARCH_WARPS;

@@ -174,3 +174,19 @@ def test_binding_enums_match_header():
                         ("constant", "CONSTANT")):
         assert lbm.WETTING[name] == decl[f"LBM_WET_{hname}"]
     assert (lbm.PAIR_CROSS, lbm.PAIR_SELF) == (decl["LBM_PAIR_CROSS"], decl["LBM_PAIR_SELF"])
+
+
+def test_size_limit_without_gpu():
+    """Padded node indices stay below 2^30 (list entries keep two tag bits
+    above them): the largest square grid under the limit is accepted (its
+    workspace holds two population buffers of 18 FP32 planes), one just
+    above it and a thin grid of 2^28 rows are rejected."""
+    lbm.load()
+    n_ok, n_bad = 32700, 32760
+    px_ok = -(-(32 + n_ok + 4) // 32) * 32
+    px_bad = -(-(32 + n_bad + 4) // 32) * 32
+    assert px_ok * (n_ok + 8) < 1 << 30 <= px_bad * (n_bad + 8)
+    assert lbm.workspace_bytes(lbm.make_params(n_ok, n_ok)) > 2 * 18 * px_ok * (n_ok + 8) * 4
+    for nx, ny in ((n_bad, n_bad), (4, 1 << 28)):
+        with pytest.raises(lbm.LbmError):
+            lbm.workspace_bytes(lbm.make_params(nx, ny))

@@ -167,6 +167,26 @@ def test_fp64_no_solid_and_isolated_fluid(kernel):
     assert max(errors(o, g, mask)) < 1e-11
 
 
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_no_fluid_node(kernel, storage):
+    """An all-solid box, walled and periodic: every schedule runs over empty
+    lists, tiles and work lists, and the state stays what the oracle keeps
+    (no mass, zero densities and velocities, no interface-solid cell)."""
+    nx, ny = 40, 20
+    mask = np.ones((ny, nx), np.uint8)
+    rA, rB, ux, uy = inputs.random_fields(nx, ny, seed=6, lo=0.2, hi=0.9, umax=0.01)
+    for periodic in ((False, False), (True, True)):
+        o, sim, g = run_pair(nx, ny, mask, rA, rB, 5, "improved", periodic=periodic, storage=storage,
+                             kernel=kernel)
+        rho, _, _, u = o.fields()
+        assert sim.interface_count() == 0
+        assert list(sim.mass()) == [0.0, 0.0] and list(o.mass()) == [0.0, 0.0]
+        for a, b in ((g[0], rho[0]), (g[1], rho[1]), (g[2], u)):
+            assert np.array_equal(a, b)
+        sim.close()
+
+
 @pytest.mark.parametrize("storage", ["fp32", "fp64"])
 def test_forces_and_populations_api(storage):
     nx, ny = 60, 40
