@@ -140,10 +140,11 @@ typedef struct {
                                  0 -> nx*ny (always enough) */
   int32_t velocity_refs;      /* 16-bit storage only: 1 stores each population
                                  as its deviation from w_i rho (1 + 3 c_i . u)
-                                 of its writer (rho and u kept in the
-                                 workspace, u as FP16: 8 more bytes per
-                                 padded node, slower, more accurate for moving
-                                 fluid); 0 (default) from w_i rho */
+                                 of its writer (per component; the writer's
+                                 rho in FP32 and u in FP16 kept in two
+                                 velocity planes, 32 more bytes per padded
+                                 node; slower, holds moving droplets far more
+                                 accurately); 0 (default) from w_i rho */
 } lbm_params;
 
 typedef struct {

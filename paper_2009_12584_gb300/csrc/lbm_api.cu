@@ -80,7 +80,7 @@ bool layout(const lbm_params* p, const Geo& g, Layout* L) {
   size_t off = 0;
   L->f = off;        off = align_up(off + 2 * 18 * (size_t)g.plane * es, A);
   L->P = off;        off = align_up(off + (tiled16(p) ? 6 : 4) * (size_t)g.plane * cs, A);
-  L->U = off;        off = align_up(off + (es == 2 && p->velocity_refs ? 2 * (size_t)g.plane * 8 : 0), A);
+  L->U = off;        off = align_up(off + (es == 2 && p->velocity_refs ? 2 * (size_t)g.plane * sizeof(UPair) : 0), A);
   L->flags = off;    off = align_up(off + (size_t)g.plane * 2, A);
   L->list = off;     off = align_up(off + (size_t)cap * 4, A);
   L->imask = off;    off = align_up(off + (size_t)cap * 4, A);
@@ -546,7 +546,7 @@ lbm_status lbm_create(const lbm_params* params, void* d_workspace, size_t bytes,
   c->Pbase = c->ws + L.P;
   const bool uplanes = es == 2 && params->velocity_refs;
   c->Ubuf[0] = uplanes ? (UPair*)(c->ws + L.U) : nullptr;
-  c->Ubuf[1] = uplanes ? (UPair*)(c->ws + L.U + (size_t)g.plane * 8) : nullptr;
+  c->Ubuf[1] = uplanes ? (UPair*)(c->ws + L.U + (size_t)g.plane * sizeof(UPair)) : nullptr;
   c->pcur = 0;
   c->P = c->Pbuf[0];
   c->p_valid = false;

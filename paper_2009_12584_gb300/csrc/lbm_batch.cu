@@ -23,7 +23,7 @@ template <typename C>
 struct BatchDesc {
   const void* f[2];
   void* Pbuf[2];
-  UPair* Ubuf[2];  // 16-bit storage: velocity part of the references of f[0] / f[1]
+  UPair* Ubuf[2];  // 16-bit storage with velocity references: writers' rho and 3 u of f[0] / f[1]
   const uint16_t* flags;
   const uint16_t* tile_entries;  // tiled schedule: the member's per-tile lists
   const int* tile_off;

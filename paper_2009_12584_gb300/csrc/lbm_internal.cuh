@@ -35,8 +35,8 @@ struct lbm_ctx {
   void* Pbuf[3];       // density plane pairs (compute type); the third only for
                        // the tiled schedule with 16-bit storage (null otherwise)
   char* Pbase;         // start of the density planes in the workspace
-  UPair* Ubuf[2];    // 16-bit storage with velocity_refs: 3 u of the writers of f[0] / f[1] (the
-                       // velocity part of the encoding references); null otherwise
+  UPair* Ubuf[2];    // 16-bit storage with velocity_refs: rho and 3 u of the writers of f[0] / f[1]
+                       // (the encoding references); null otherwise
   void* P;             // Pbuf[pcur]: the densities the current populations were
                        // written with (16-bit encoding references); after a
                        // single-pass step, the densities of the current state

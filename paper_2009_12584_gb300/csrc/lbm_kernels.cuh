@@ -42,34 +42,42 @@ __device__ __forceinline__ void prefetch_list_ahead(const int* __restrict__ list
 //  - with velocity references (lbm_params.velocity_refs), w_d rho^s
 //    (1 + c_d . U^s) with U^s = 3 j*^s / rho^s, j*^s the momentum of the
 //    populations the writer stored (post-collision), rounded to FP16 and
-//    kept in a velocity plane Uref: the reference then carries the first
-//    moment of what was written (the equilibrium's velocity term and the
-//    Guo source's first-order term), and the deviation only the rest.
+//    kept with the writer's rho^s in a velocity plane Uref (one 16-byte
+//    element per node): the reference then carries the first moment of
+//    what was written (the equilibrium's velocity term and the Guo source's
+//    first-order term), and the deviation only the rest.
 // The 11 (FP16) or 8 (BF16) significand bits go to what varies. For 4- and
 // 8-byte storage the references are zero and the planes are not read.
 template <typename T>
 constexpr bool kDev = sizeof(T) == 2;
 
-// Element of a velocity plane: (U^A, U^B) as two FP16 pairs.
-using UPair = uint2;
+// Element of a velocity plane (16 bytes, one load): the writer's rho^A and
+// rho^B in FP32 (the densities it encoded with) and its U^A, U^B as two
+// FP16 pairs.
+using UPair = uint4;
 struct UVal {
   float2 v[2];  // U^A, U^B
+  float r[2];   // rho^A, rho^B
 };
 __device__ __forceinline__ UVal u_unpack(UPair p) {
   UVal u;
-  u.v[0] = __half22float2(*reinterpret_cast<const __half2*>(&p.x));
-  u.v[1] = __half22float2(*reinterpret_cast<const __half2*>(&p.y));
+  u.r[0] = __uint_as_float(p.x);
+  u.r[1] = __uint_as_float(p.y);
+  u.v[0] = __half22float2(*reinterpret_cast<const __half2*>(&p.z));
+  u.v[1] = __half22float2(*reinterpret_cast<const __half2*>(&p.w));
   return u;
 }
-// U^s = 3 j^s / rho^s of both components, rounded to FP16 (jx, jy, rho:
-// component A in .x, B in .y).
+// The element of a writer with densities rho and momenta (jx, jy)
+// (component A in .x, B in .y): U^s = 3 j^s / rho^s rounded to FP16.
 __device__ __forceinline__ UPair u_pack(float2 jx, float2 jy, float2 rho) {
   const float ia = rho.x > 0.0f ? 3.0f / rho.x : 0.0f, ib = rho.y > 0.0f ? 3.0f / rho.y : 0.0f;
   const __half2 a = __floats2half2_rn(jx.x * ia, jy.x * ia);
   const __half2 b = __floats2half2_rn(jx.y * ib, jy.y * ib);
   UPair p;
-  p.x = *reinterpret_cast<const unsigned*>(&a);
-  p.y = *reinterpret_cast<const unsigned*>(&b);
+  p.x = __float_as_uint(rho.x);
+  p.y = __float_as_uint(rho.y);
+  p.z = *reinterpret_cast<const unsigned*>(&a);
+  p.w = *reinterpret_cast<const unsigned*>(&b);
   return p;
 }
 
@@ -102,13 +110,11 @@ __device__ __forceinline__ void pull_refs(const C* __restrict__ Pref, const UPai
       for (int i = 0; i < 9; ++i) {
         const bool self = i == 0 || (check && (fl & nb_bit(opp_of(i))));
         const int m = self ? k : k - cx_of(i) - cy_of(i) * g.px;
-        C a, b;
-        ldP(Pref, m, a, b);
-        const UVal u = u_unpack(__ldg(Uref + m));
-        const bool back = self && i != 0;  // the value was sent along -c_i
+        const UVal u = u_unpack(__ldg(Uref + m));  // the writer's densities and velocities
+        const bool back = self && i != 0;          // the value was sent along -c_i
         const float ca = cdot(i, u.v[0]), cb = cdot(i, u.v[1]);
-        ref[0][i] = ref_of(i, a, back ? -ca : ca);
-        ref[1][i] = ref_of(i, b, back ? -cb : cb);
+        ref[0][i] = ref_of(i, u.r[0], back ? -ca : ca);
+        ref[1][i] = ref_of(i, u.r[1], back ? -cb : cb);
       }
     } else {
 #pragma unroll
@@ -680,8 +686,13 @@ __global__ void __launch_bounds__(256) k_mass_partial(const T* __restrict__ f,
     C rw[2] = {C(0), C(0)};
     UVal U{};
     if (kDev<T>) {
-      ldP(Pref, k, rw[0], rw[1]);
-      if (Uref) U = u_unpack(Uref[k]);
+      if (Uref) {
+        U = u_unpack(Uref[k]);
+        rw[0] = U.r[0];
+        rw[1] = U.r[1];
+      } else {
+        ldP(Pref, k, rw[0], rw[1]);
+      }
     }
     C ref[2][9];
     write_refs<T>(rw, Uref != nullptr, U, ref);
