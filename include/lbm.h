@@ -104,16 +104,17 @@ typedef enum {
  *   storage runs TWO_PASS); the workspace grows by about 4 bytes per node.
  *   The fastest schedule under Martys-Chen, LLKC and the constant solid
  *   density (one ring); slower than TILED under the improved scheme.
- * TMA: the TILED schedule (same lists, same results bit for bit) with a
- *   persistent CTA per SM walking a list of the tiles that own fluid nodes;
- *   each tile's inputs, the nine population planes and the density plane
- *   over its (32 + 4) x (14 + 4) window and its entry list, are copied into
- *   shared memory by the Tensor Memory Accelerator into a three-stage ring,
- *   two tiles ahead of the update. FP32 storage (other storage runs TILED);
- *   the workspace grows by 16 bytes per tile. A copy not seen to complete
- *   within about a second stops the kernel and is reported as
- *   LBM_ERR_TIMEOUT by the next lbm_sync, lbm_mass or lbm_step_profiled.
- *   Slower than TILED on GB300 (one tile per SM at a time).
+ * TMA: the TILED schedule (same lists, same results bit for bit) with two
+ *   persistent CTAs per SM walking a list of the tiles that own fluid
+ *   nodes; each tile's inputs, the nine population planes and the density
+ *   plane over its (32 + 4) x (14 + 4) window and its entry list, are
+ *   copied into shared memory by the Tensor Memory Accelerator into a
+ *   two-stage ring, one tile ahead of the update. FP32 storage (other
+ *   storage runs TILED); the workspace grows by 16 bytes per tile. A copy
+ *   not seen to complete within about a second stops the kernel and is
+ *   reported as LBM_ERR_TIMEOUT by the next lbm_sync, lbm_mass or
+ *   lbm_step_profiled. Slower than TILED on GB300 (the windows also carry
+ *   the solid slots that the tiled kernel's lists skip).
  * AUTO picks the schedule measured fastest on GB300: TILED for 4- and 8-byte
  * storage (a quarter fewer bytes than TWO_PASS and 8% faster on the 8192^2
  * porous medium; its lists are then built as for TILED), TWO_PASS for 16-bit

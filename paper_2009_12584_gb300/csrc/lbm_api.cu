@@ -52,7 +52,9 @@ bool uses_tiles(const lbm_params* p) {
 }
 
 // Whether the TMA variant of the tiled schedule runs (FP32 storage).
-bool uses_tma(const lbm_params* p) { return p->kernel == LBM_KERNEL_TMA && p->storage == LBM_STORE_FP32; }
+bool uses_tma(const lbm_params* p) {
+  return TMA_AVAILABLE && p->kernel == LBM_KERNEL_TMA && p->storage == LBM_STORE_FP32;
+}
 
 // Whether a context keeps the per-tile lists of the halo schedule (4- and
 // 8-byte storage; 16-bit storage runs the two-pass schedule instead).
@@ -308,7 +310,9 @@ lbm_status step_fused(lbm_ctx* c, int nsteps) {
             c->tma_smem_set = true;
           }
           const int ntx = (c->g.nx + TILE_W - 1) / TILE_W;
-          const int grid = c->n_work < c->num_sms ? (c->n_work > 0 ? c->n_work : 1) : c->num_sms;
+          // TMA_MINB persistent CTAs per SM
+          const int slots = c->num_sms * TMA_MINB;
+          const int grid = c->n_work < slots ? (c->n_work > 0 ? c->n_work : 1) : slots;
           k_tile_tma<<<grid, TMA_THREADS, SMEM, c->stream>>>(
               c->tmap_f[c->cur], c->tmap_P[c->pcur], (float*)fout, (float*)Pout, c->flags, c->tile_entries,
               c->tile_work, c->n_work, c->g, ntx, kphys<float>(c->ph), c->small + 4);

@@ -30,13 +30,24 @@ constexpr int TMA_BOX_X = 2 * TMA_WW;               // floats per window row (co
 constexpr int TMA_PLANE_BYTES = TMA_BOX_X * TMA_WH * 4;
 constexpr int TMA_SLOT_BYTES = (TMA_PLANE_BYTES + 127) / 128 * 128;  // 128-byte aligned destinations
 constexpr int TMA_ENTRY_BYTES = (TILE_RS + 7) / 8 * 16;  // a tile's list, padded to 8 entries
-constexpr int TMA_NBUF = 3;
 // nine population planes, the density plane and the entries, 128-byte aligned
 constexpr int TMA_BUF_BYTES = (10 * TMA_SLOT_BYTES + TMA_ENTRY_BYTES + 127) / 128 * 128;
 #ifndef LBM_TMA_THREADS
-#define LBM_TMA_THREADS 512
+#define LBM_TMA_THREADS 0  // 0: one thread per region slot, rounded up to a warp
 #endif
-constexpr int TMA_THREADS = LBM_TMA_THREADS;
+#ifndef LBM_TMA_NBUF
+#define LBM_TMA_NBUF 2
+#endif
+#ifndef LBM_TMA_MINB
+#define LBM_TMA_MINB 2
+#endif
+constexpr int TMA_THREADS = LBM_TMA_THREADS > 0 ? LBM_TMA_THREADS : (TILE_RS + 31) / 32 * 32;
+constexpr int TMA_NBUF = LBM_TMA_NBUF;  // copy stages per CTA (tiles in flight: NBUF - 1 ahead)
+constexpr int TMA_MINB = LBM_TMA_MINB;  // CTAs per SM (registers and shared memory must allow it)
+// One node per thread, and f*(t+1) of the region written over the consumed
+// window: the schedule exists for tile shapes whose region fits both (else
+// LBM_KERNEL_TMA runs the tiled schedule).
+constexpr bool TMA_AVAILABLE = TILE_RS <= TMA_THREADS && 9 * TILE_RS * 8 <= 10 * TMA_SLOT_BYTES;
 // Nanoseconds (of the global timer) a CTA waits for a tile's copies before
 // it gives up and reports them: far above any copy's latency, short enough
 // to return control to the host within about a second.
@@ -47,7 +58,7 @@ static_assert(TILE_W % 2 == 0, "window x starts must be 16-byte aligned: 4 * 2 *
 
 template <typename T>
 constexpr size_t tma_smem() {
-  return TMA_NBUF * (size_t)TMA_BUF_BYTES + (size_t)9 * TILE_RS * sizeof(float2) + 128;
+  return TMA_NBUF * (size_t)TMA_BUF_BYTES + 128;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -171,21 +182,31 @@ __device__ __forceinline__ void tma_issue(unsigned char* buf, uint64_t* bar, con
   bulk_load(buf + 10 * TMA_SLOT_BYTES, entries + w.y, ebytes, bar);
 }
 
+
+// Persistent CTAs walk the work list with a stride of the grid, TMA_MINB per
+// SM; the copies of each CTA's next TMA_NBUF - 1 tiles are in flight while it
+// updates the current one. One thread per listed node (TILE_RS <= threads):
+// phase 1 reads the window and keeps f*(t+1) in registers, the CTA waits for
+// every read of the window, writes f*(t+1) over it ([9][TILE_RS] pairs at
+// the buffer's start; the entry list after the planes stays), waits again,
+// and phase 2 sums rho(t+1) of the owned nodes from there.
 // err: set to 1 when a copy was not seen to complete within the bound (the
 // CTA then stops). The host reads it at its next synchronising call.
-static __global__ void __launch_bounds__(TMA_THREADS, 1)
+static __global__ void __launch_bounds__(TMA_THREADS, TMA_MINB)
     k_tile_tma(const __grid_constant__ CUtensorMap mapf, const __grid_constant__ CUtensorMap mapP,
                float* __restrict__ fo, float* __restrict__ Po, const uint16_t* __restrict__ flags,
                const uint16_t* __restrict__ entries, const int4* __restrict__ work, int n_work, Geo g, int ntx,
                PhysK<float> ph, int* __restrict__ err) {
+  if constexpr (!TMA_AVAILABLE) {
+    return;  // never launched (the host runs the tiled schedule instead)
+  } else {
   using V = float2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  V* s = reinterpret_cast<V*>(base + TMA_NBUF * TMA_BUF_BYTES);  // f*(t+1) of the region, [9][TILE_RS]
   __shared__ __align__(8) uint64_t bar[TMA_NBUF];
   const float zr[2][9] = {};  // storage references: zero for 4-byte populations
   const int G = gridDim.x;
-  int4 wnext = make_int4(-1, 0, 0, 0);  // thread 0: the item two ahead of the current one
+  int4 wnext = make_int4(-1, 0, 0, 0);  // thread 0: the work item TMA_NBUF - 1 ahead of the current one
   if (threadIdx.x == 0) {
     for (int b = 0; b < TMA_NBUF; ++b) mbar_init(&bar[b], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -197,14 +218,15 @@ static __global__ void __launch_bounds__(TMA_THREADS, 1)
     if (w2 < n_work) wnext = __ldg(work + w2);
   }
   __syncthreads();
+  const int t = threadIdx.x;
   for (int n = 0;; ++n) {
     const int wn = blockIdx.x + n * G;
     if (wn >= n_work) break;
     const int cur = n % TMA_NBUF;
     unsigned char* buf = base + cur * TMA_BUF_BYTES;
-    if (threadIdx.x == 0) {
+    if (t == 0) {
       // the item TMA_NBUF - 1 ahead into the buffer the previous iteration
-      // freed (its closing barrier), then the item after it towards a register
+      // freed (its closing barrier)
       const int wa = wn + (TMA_NBUF - 1) * G;
       if (wa < n_work) {
         const int ba = (n + TMA_NBUF - 1) % TMA_NBUF;
@@ -217,7 +239,7 @@ static __global__ void __launch_bounds__(TMA_THREADS, 1)
     if (__syncthreads_or(!ok)) {
       // a copy did not complete within the bound: report it and stop this
       // CTA after waiting (bounded) for the copies it has in flight
-      if (threadIdx.x == 0) {
+      if (t == 0) {
         atomicExch(err, 1);
         for (int k = n; k < n + TMA_NBUF; ++k)
           if (blockIdx.x + k * G < n_work) mbar_wait(&bar[k % TMA_NBUF], (uint32_t)((k / TMA_NBUF) & 1));
@@ -229,20 +251,19 @@ static __global__ void __launch_bounds__(TMA_THREADS, 1)
     const int tile = item.x, n_all = item.z, n_own = item.w;
     const int x0 = (tile % ntx) * TILE_W, y0 = (tile / ntx) * TILE_H;
     const int korg = g.idx(x0 - 1, y0 - 1);  // padded index of region slot 0
-    for (int b = 0; b < n_all; b += TMA_THREADS) {
-      const int t = b + threadIdx.x;
-      const bool valid = t < n_all;
-      const uint16_t e = valid ? ent[t] : uint16_t(0);
-      const bool warp_edge = __any_sync(0xffffffffu, (e & TE_SOLIDNB) != 0);
-      const bool warp_border = __any_sync(0xffffffffu, (e & TE_BORDER) != 0);
-      if (!valid) continue;
-      const int slot = e & TE_SLOT;
-      const int row = slot / TILE_RW, col = slot - row * TILE_RW;
-      const int k = korg + row * g.px + col;
+    const bool valid = t < n_all;
+    const uint16_t e = valid ? ent[t] : uint16_t(0);
+    const bool warp_edge = __any_sync(0xffffffffu, (e & TE_SOLIDNB) != 0);
+    const bool warp_border = __any_sync(0xffffffffu, (e & TE_BORDER) != 0);
+    const int slot = e & TE_SLOT;
+    const int row = slot / TILE_RW, col = slot - row * TILE_RW;
+    const int k = korg + row * g.px + col;
+    float fv[2][9];
+    if (valid) {
       const uint16_t fl = warp_edge ? __ldg(flags + k) : uint16_t(0);
       // region slot (row, col) is window pair (row + 1, col + 1)
       const int wc = (row + 1) * TMA_BOX_X + 2 * (col + 1);
-      float fv[2][9], nbP[2][9];
+      float nbP[2][9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
         const V v = *reinterpret_cast<const V*>(win + i * (TMA_SLOT_BYTES / 4) + wc - cy_of(i) * TMA_BOX_X -
@@ -271,15 +292,15 @@ static __global__ void __launch_bounds__(TMA_THREADS, 1)
           store_bounced(fo, g, x, y, fl, fv, zr);
         }
       }
+    }
+    __syncthreads();  // every read of the window is done: f*(t+1) goes over it
+    V* s = reinterpret_cast<V*>(buf);
+    if (valid) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) s[i * TILE_RS + slot] = make_float2(fv[0][i], fv[1][i]);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < n_own; t += TMA_THREADS) {
-      const uint16_t e = ent[t];
-      const int slot = e & TE_SLOT;
-      const int row = slot / TILE_RW, col = slot - row * TILE_RW;
-      const int k = korg + row * g.px + col;
+    if (t < n_own) {
       const uint16_t fl = (e & TE_SOLIDNB) ? __ldg(flags + k) : uint16_t(0);
       float fn[2][9];
 #pragma unroll
@@ -296,7 +317,11 @@ static __global__ void __launch_bounds__(TMA_THREADS, 1)
         for_ghost_images(g, x, y, [&](int kk) { stP(Po, kk, r0, r1); });
       }
     }
-    __syncthreads();  // this tile's buffer and the f*(t+1) region are free
+    // this thread's generic accesses to the buffer before the copies that
+    // will overwrite it (issued after the barrier)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();  // the buffer is free
+  }
   }
 }
 
