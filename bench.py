@@ -528,7 +528,10 @@ def main():
     sched = effective_schedule(args.kernel, args.storage)
     tkey = dom if dom != "fused" else {"tiled": "tile", "fused": "march"}.get(sched, sched)
     traffic = measured_traffic(tkey, args.storage, l2_fetch)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
+    kernel_name = {"tile": "k_tile", "march": "k_march", "halo": "k_halo", "tma": "k_tile_tma",
+                   "collide": "k_collide_list", "density": "k_density_list"}.get(tkey, tkey)
+    roofline = {"bound": "hbm", "kernel": dom, "kernel_name": kernel_name, "achieved": round(achieved, 1),
+                "peak": pk["hbm_gbs"],
                 "peak_kind": pk_kind, "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
                 "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
                 "per_launch_ms": round(per_launch_ms, 4),
