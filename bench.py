@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import subprocess
@@ -63,11 +64,17 @@ def workload(n, cache=True):
 
 
 def source_hash():
+    """Hash of the CUDA sources' code: comments and whitespace are dropped,
+    so that a change of wording does not invalidate the recorded traffic,
+    and every change of code does."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2009_12584_gb300", "csrc")
     for name in sorted(os.listdir(d)):
         if name.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, name), "rb").read())
+            text = open(os.path.join(d, name), encoding="utf-8").read()
+            text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+            text = re.sub(r"//[^\n]*", " ", text)
+            h.update(name.encode() + b"\0" + " ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

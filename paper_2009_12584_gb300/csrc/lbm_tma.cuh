@@ -4,18 +4,19 @@
 //
 // k_tile pulls every population of every listed node with its own load and
 // waits for them (list entry -> pulls -> update is a chain of dependent
-// global round trips per node). Here a persistent CTA (one per SM) walks a
-// work list of the tiles that own fluid nodes (items blockIdx.x,
-// + gridDim.x, ...) and, while it updates one tile, the TMA copies the next
-// two tiles' inputs into the other two thirds of a triple buffer: the nine
-// population planes and the density plane over the (TILE_W + 4) x
-// (TILE_H + 4) window that the tile and its one-node ring pull from (ten
-// 2-D boxes) and the tile's list entries (one 1-D bulk copy; the lists are
-// padded to 16-byte boundaries). No per-node address arithmetic, no
-// registers held by loads in flight, no dependent global load before a
-// tile's update. An mbarrier per buffer counts the bytes in; the wait on it
-// is bounded (TMA_WAIT_NS). Stores, the ring, phase 2 and the periodic
-// images are those of k_tile.
+// global round trips per node). Here persistent CTAs (TMA_MINB per SM) walk
+// a work list of the tiles that own fluid nodes (items blockIdx.x,
+// + gridDim.x, ...) and, while a CTA updates one tile, the TMA copies its
+// next tile's inputs into the other stage of a ring of TMA_NBUF buffers: the
+// nine population planes and the density plane over the (TILE_W + 4) x
+// (TILE_H + 4) window that the tile and its one-node ring pull from (nine
+// 3-D boxes and one 2-D box) and the tile's list entries (one 1-D bulk copy;
+// the lists are padded to 16-byte boundaries). No per-node address
+// arithmetic for the loads, no registers held by loads in flight, no
+// dependent global load before a tile's update. An mbarrier per buffer
+// counts the bytes in; the wait on it is bounded (TMA_WAIT_NS). One thread
+// per region slot; f*(t+1) is written over the consumed window. Stores, the
+// ring, phase 2 and the periodic images are those of k_tile.
 #pragma once
 
 #include <cuda.h>  // CUtensorMap
