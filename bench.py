@@ -541,6 +541,8 @@ def main():
                 "peak": pk["hbm_gbs"],
                 "peak_kind": pk_kind, "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
                 "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
+                "algorithmic_bytes_per_update": bpu,
+                "traffic_bytes_per_update": None if traffic is None else round(traffic / nf, 1),
                 "per_launch_ms": round(per_launch_ms, 4),
                 "kernel_ms_per_step": {k: round(v / args.steps, 4) for k, v in ms_cls.items() if cnt_cls[k]}}
 
