@@ -250,6 +250,17 @@ lbm_status lbm_mass(lbm_ctx* ctx, double* h_out);
  * paper has no counterpart. */
 lbm_status lbm_set_l2_fetch_granularity(int32_t bytes, int32_t* previous);
 
+/* Test hook of the TMA schedule's bounded wait (not for production use):
+ * from the next step on, the barrier of every tile's copies expects `bytes`
+ * (0 ... 4096) more than the copies deliver, so that its wait runs out
+ * after about a second, each CTA stops after waiting (bounded) for the
+ * copies it has in flight, and the next lbm_sync, lbm_mass or
+ * lbm_step_profiled returns LBM_ERR_TIMEOUT; the populations of that step
+ * are then incomplete (re-initialise or restore them). 0, the default,
+ * restores normal operation. No effect on other schedules. LBM_ERR_ARG for
+ * a null context or a size out of range. */
+lbm_status lbm_debug_tma_expect_extra(lbm_ctx* ctx, int32_t bytes);
+
 /* ---- On-device diagnostics ----------------------------------------------
  * The measurements of Secs. 3-4 of arXiv:2009.12584, reduced on the device
  * from the current moments (rho^A, u of Eq. 3) so that long runs copy no

@@ -315,7 +315,7 @@ lbm_status step_fused(lbm_ctx* c, int nsteps) {
           const int grid = c->n_work < slots ? (c->n_work > 0 ? c->n_work : 1) : slots;
           k_tile_tma<<<grid, TMA_THREADS, SMEM, c->stream>>>(
               c->tmap_f[c->cur], c->tmap_P[c->pcur], (float*)fout, (float*)Pout, c->flags, c->tile_entries,
-              c->tile_work, c->n_work, c->g, ntx, kphys<float>(c->ph), c->small + 4);
+              c->tile_work, c->n_work, c->g, ntx, kphys<float>(c->ph), c->small + 4, c->tma_extra_tx);
         });
         if (ls) return fail(c, ls, "k_tile_tma launch rejected");
         if (s) return s;
@@ -511,6 +511,12 @@ const char* lbm_status_str(lbm_status s) {
 const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err : ""; }
 
 int64_t lbm_launch_count(const lbm_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+lbm_status lbm_debug_tma_expect_extra(lbm_ctx* c, int32_t bytes) {
+  if (!c || bytes < 0 || bytes > 4096) return LBM_ERR_ARG;
+  c->tma_extra_tx = (uint32_t)bytes;
+  return LBM_OK;
+}
 
 lbm_status lbm_workspace_bytes(const lbm_params* params, size_t* bytes) {
   if (!valid_params(params) || !bytes) return LBM_ERR_ARG;

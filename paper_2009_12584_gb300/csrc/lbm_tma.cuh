@@ -163,9 +163,11 @@ static __global__ void __launch_bounds__(1024)
 
 // Issue the copies of work item w (tile's window and entries) into buffer
 // `buf` (one thread).
+// extra_tx: bytes the barrier expects beyond what the copies deliver (0;
+// the test of the bounded wait sets it so that the wait runs out).
 __device__ __forceinline__ void tma_issue(unsigned char* buf, uint64_t* bar, const CUtensorMap* mapf,
                                           const CUtensorMap* mapP, const uint16_t* __restrict__ entries, int4 w,
-                                          int ntx) {
+                                          int ntx, uint32_t extra_tx) {
   const int tile = w.x;
   const int x0 = (tile % ntx) * TILE_W, y0 = (tile / ntx) * TILE_H;
   // padded coordinates of the window's first pair: column x0 - 2 + LP (its
@@ -176,7 +178,7 @@ __device__ __forceinline__ void tma_issue(unsigned char* buf, uint64_t* bar, con
   // order the generic-proxy reads of this buffer (three tiles back) before
   // the copies' writes
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  mbar_expect_tx(bar, 10u * TMA_PLANE_BYTES + ebytes);
+  mbar_expect_tx(bar, 10u * TMA_PLANE_BYTES + ebytes + extra_tx);
 #pragma unroll
   for (int i = 0; i < 9; ++i) tma_load_3d(buf + i * TMA_SLOT_BYTES, mapf, xf, yw, i, bar);
   tma_load_2d(buf + 9 * TMA_SLOT_BYTES, mapP, xf, yw, bar);
@@ -193,11 +195,12 @@ __device__ __forceinline__ void tma_issue(unsigned char* buf, uint64_t* bar, con
 // and phase 2 sums rho(t+1) of the owned nodes from there.
 // err: set to 1 when a copy was not seen to complete within the bound (the
 // CTA then stops). The host reads it at its next synchronising call.
+// extra_tx: see tma_issue (0 in operation).
 static __global__ void __launch_bounds__(TMA_THREADS, TMA_MINB)
     k_tile_tma(const __grid_constant__ CUtensorMap mapf, const __grid_constant__ CUtensorMap mapP,
                float* __restrict__ fo, float* __restrict__ Po, const uint16_t* __restrict__ flags,
                const uint16_t* __restrict__ entries, const int4* __restrict__ work, int n_work, Geo g, int ntx,
-               PhysK<float> ph, int* __restrict__ err) {
+               PhysK<float> ph, int* __restrict__ err, uint32_t extra_tx) {
   if constexpr (!TMA_AVAILABLE) {
     return;  // never launched (the host runs the tiled schedule instead)
   } else {
@@ -213,7 +216,8 @@ static __global__ void __launch_bounds__(TMA_THREADS, TMA_MINB)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int k = 0; k < TMA_NBUF - 1; ++k) {
       const int wk = blockIdx.x + k * G;
-      if (wk < n_work) tma_issue(base + k * TMA_BUF_BYTES, &bar[k], &mapf, &mapP, entries, __ldg(work + wk), ntx);
+      if (wk < n_work)
+        tma_issue(base + k * TMA_BUF_BYTES, &bar[k], &mapf, &mapP, entries, __ldg(work + wk), ntx, extra_tx);
     }
     const int w2 = blockIdx.x + (TMA_NBUF - 1) * G;
     if (w2 < n_work) wnext = __ldg(work + w2);
@@ -231,7 +235,7 @@ static __global__ void __launch_bounds__(TMA_THREADS, TMA_MINB)
       const int wa = wn + (TMA_NBUF - 1) * G;
       if (wa < n_work) {
         const int ba = (n + TMA_NBUF - 1) % TMA_NBUF;
-        tma_issue(base + ba * TMA_BUF_BYTES, &bar[ba], &mapf, &mapP, entries, wnext, ntx);
+        tma_issue(base + ba * TMA_BUF_BYTES, &bar[ba], &mapf, &mapP, entries, wnext, ntx, extra_tx);
         if (wa + G < n_work) wnext = __ldg(work + wa + G);
       }
     }

@@ -67,7 +67,7 @@ EXPORTS = [
     "lbm_workspace_bytes", "lbm_create", "lbm_set_stream", "lbm_set_geometry", "lbm_set_wetting",
     "lbm_init_fields", "lbm_step", "lbm_step_profiled", "lbm_moments", "lbm_forces", "lbm_get_populations",
     "lbm_set_populations", "lbm_mass", "lbm_diagnostics", "lbm_set_l2_fetch_granularity", "lbm_interface_count",
-    "lbm_sync", "lbm_run_host", "lbm_run_host_f32",
+    "lbm_sync", "lbm_run_host", "lbm_run_host_f32", "lbm_debug_tma_expect_extra",
     "lbm_destroy", "lbm_status_str", "lbm_last_error", "lbm_launch_count",
     "lbm_batch_workspace_bytes", "lbm_batch_create", "lbm_batch_set_graph_steps", "lbm_batch_step",
     "lbm_batch_autotune", "lbm_batch_set_schedule", "lbm_batch_config", "lbm_batch_launch_count",
@@ -122,6 +122,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "lbm_set_l2_fetch_granularity": [i32, ctypes.POINTER(i32)],
             "lbm_interface_count": [vp, ctypes.POINTER(i64)],
             "lbm_sync": [vp],
+            "lbm_debug_tma_expect_extra": [vp, i32],
             "lbm_run_host": [vp, W, vp, vp, vp, i32, vp, vp, vp, vp],
             "lbm_run_host_f32": [vp, W, vp, vp, vp, i32, vp, vp, vp, vp],
             "lbm_destroy": [vp],
@@ -343,6 +344,11 @@ class Simulation:
 
     def sync(self):
         self._check(self.lib.lbm_sync(self.h), "lbm_sync")
+
+    def debug_tma_expect_extra(self, nbytes):
+        """Test hook of the TMA schedule's bounded wait (see lbm.h)."""
+        self._check(self.lib.lbm_debug_tma_expect_extra(self.h, int(nbytes)), "lbm_debug_tma_expect_extra")
+        return self
 
     @property
     def launch_count(self):

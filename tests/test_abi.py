@@ -105,6 +105,9 @@ def test_argument_checks_before_any_cuda_call(lib):
     lib.lbm_diagnostics.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.lbm_diagnostics.restype = ctypes.c_int
     assert lib.lbm_diagnostics(None, None, None) == lbm.ERR_ARG
+    lib.lbm_debug_tma_expect_extra.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    lib.lbm_debug_tma_expect_extra.restype = ctypes.c_int
+    assert lib.lbm_debug_tma_expect_extra(None, 16) == lbm.ERR_ARG
 
 
 def test_tiled_schedule_workspace_without_gpu():
