@@ -79,9 +79,11 @@ def source_hash():
 
 
 def effective_schedule(kernel, storage):
-    """The schedule lbm_step runs: AUTO takes the tiled one for 4- and 8-byte
-    storage and the two-pass one for 16-bit storage; 16-bit storage runs a
-    FUSED choice as two-pass too (the marching kernel has no 16-bit path)."""
+    """The schedule lbm_step runs on the benchmark workload (improved scheme):
+    AUTO takes the tiled one for 4- and 8-byte storage (the halo one only
+    under the one-node-reach schemes) and the two-pass one for 16-bit
+    storage; 16-bit storage runs a FUSED choice as two-pass too (the
+    marching kernel has no 16-bit path)."""
     if storage in ("fp16", "bf16"):
         return "tiled" if kernel == "tiled" else "two_pass"
     return "tiled" if kernel == "auto" else kernel

@@ -115,10 +115,13 @@ typedef enum {
  *   reported as LBM_ERR_TIMEOUT by the next lbm_sync, lbm_mass or
  *   lbm_step_profiled. Slower than TILED on GB300 (the windows also carry
  *   the solid slots that the tiled kernel's lists skip).
- * AUTO picks the schedule measured fastest on GB300: TILED for 4- and 8-byte
- * storage (a quarter fewer bytes than TWO_PASS and 8% faster on the 8192^2
- * porous medium; its lists are then built as for TILED), TWO_PASS for 16-bit
- * storage. */
+ * AUTO picks the schedule measured fastest on GB300, at each step from the
+ * installed wetting scheme: for 4- and 8-byte storage TILED under the
+ * improved scheme (a quarter fewer bytes than TWO_PASS and 8% faster on the
+ * 8192^2 porous medium) and HALO under Martys-Chen, LLKC and the constant
+ * solid density (6% faster than TILED there); the workspace keeps both sets
+ * of lists and the halo lists are built at the first step that needs them.
+ * TWO_PASS for 16-bit storage. */
 typedef enum {
   LBM_KERNEL_AUTO = 0,
   LBM_KERNEL_TWO_PASS = 1,

@@ -57,10 +57,13 @@ bool uses_tma(const lbm_params* p) {
 }
 
 // Whether a context keeps the per-tile lists of the halo schedule (4- and
-// 8-byte storage; 16-bit storage runs the two-pass schedule instead).
+// 8-byte storage; 16-bit storage runs the two-pass schedule instead). AUTO
+// keeps room for them: it runs the halo schedule under the wetting schemes
+// whose force reaches one node (Martys-Chen, LLKC, constant rho_s), where
+// it is the fastest, and builds the lists at the first such step.
 bool uses_halo(const lbm_params* p) {
   const bool wide = p->storage == LBM_STORE_FP32 || p->storage == LBM_STORE_FP64;
-  return p->kernel == LBM_KERNEL_HALO && wide;
+  return (p->kernel == LBM_KERNEL_HALO || p->kernel == LBM_KERNEL_AUTO) && wide;
 }
 
 // The tiled schedule with 16-bit storage keeps a third density plane: a step
@@ -396,6 +399,26 @@ lbm_status step_tiled16(lbm_ctx* c, int nsteps) {
   return LBM_OK;
 }
 
+// Per-tile lists of the halo schedule for the current geometry: counts and
+// fluid bitmasks, offsets (fixed-order scan, total at halo_off[n_halo_tiles]),
+// entries. Built by lbm_set_geometry for HALO, at the first halo step for AUTO.
+lbm_status build_halo_lists(lbm_ctx* c) {
+  const Geo& g = c->g;
+  const int ntx = (g.nx + HALO_W - 1) / HALO_W;
+  const int nt = (int)c->n_halo_tiles;
+  lbm_status s;
+  k_halo_lists<<<nt, HALO_LIST_THREADS, 0, c->stream>>>(c->flags, g, ntx, nullptr, c->halo_off, c->halo_cnt,
+                                                        c->halo_fmask, nullptr);
+  if ((s = after_launch(c, "k_halo_lists(count)"))) return s;
+  k_iface_scan<<<1, 1024, 0, c->stream>>>(c->halo_off, nt, c->halo_off + nt);
+  if ((s = after_launch(c, "k_iface_scan(halo)"))) return s;
+  k_halo_lists<<<nt, HALO_LIST_THREADS, 0, c->stream>>>(c->flags, g, ntx, c->halo_off, nullptr, nullptr, nullptr,
+                                                        c->halo_entries);
+  if ((s = after_launch(c, "k_halo_lists(write)"))) return s;
+  c->halo_built = true;
+  return LBM_OK;
+}
+
 // Halo schedule: one kernel per step, densities recomputed per tile from the
 // populations (no density plane).
 template <typename T>
@@ -419,7 +442,16 @@ lbm_status step_halo(lbm_ctx* c, int nsteps) {
 template <typename T>
 lbm_status do_step(lbm_ctx* c, int nsteps) {
   if constexpr (sizeof(T) >= 4) {  // the marching kernel stores 4- and 8-byte populations only
-    if (c->n_halo_tiles > 0) return step_halo<T>(c, nsteps);
+    // HALO always; AUTO under the one-node-reach schemes (the improved
+    // scheme's Eq. 8 reaches three rings, where the tiled schedule wins)
+    const bool halo = c->prm.kernel == LBM_KERNEL_HALO || (c->prm.kernel == LBM_KERNEL_AUTO && c->ph.bc != BC_VAVG);
+    if (halo && c->n_halo_tiles > 0) {
+      if (!c->halo_built) {
+        lbm_status s = build_halo_lists(c);
+        if (s) return s;
+      }
+      return step_halo<T>(c, nsteps);
+    }
     if (c->prm.kernel == LBM_KERNEL_FUSED && fused_supported<T>(c->g, c->ph)) return step_fused<T>(c, nsteps);
     const bool tiled = c->prm.kernel == LBM_KERNEL_TILED || c->prm.kernel == LBM_KERNEL_AUTO || c->prm.kernel == LBM_KERNEL_TMA;
     if (tiled && c->n_tiles > 0) return step_fused<T>(c, nsteps);
@@ -682,20 +714,8 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* d_mask) {
       c->n_work = nw;
     }
   }
-  if (c->n_halo_tiles > 0) {
-    // per-tile lists of the halo schedule: counts and fluid bitmasks,
-    // offsets (fixed-order scan, total at halo_off[n_halo_tiles]), entries
-    const int ntx = (g.nx + HALO_W - 1) / HALO_W;
-    const int nt = (int)c->n_halo_tiles;
-    k_halo_lists<<<nt, HALO_LIST_THREADS, 0, c->stream>>>(c->flags, g, ntx, nullptr, c->halo_off, c->halo_cnt,
-                                                          c->halo_fmask, nullptr);
-    if ((s = after_launch(c, "k_halo_lists(count)"))) return s;
-    k_iface_scan<<<1, 1024, 0, c->stream>>>(c->halo_off, nt, c->halo_off + nt);
-    if ((s = after_launch(c, "k_iface_scan(halo)"))) return s;
-    k_halo_lists<<<nt, HALO_LIST_THREADS, 0, c->stream>>>(c->flags, g, ntx, c->halo_off, nullptr, nullptr, nullptr,
-                                                          c->halo_entries);
-    if ((s = after_launch(c, "k_halo_lists(write)"))) return s;
-  }
+  c->halo_built = false;
+  if (c->n_halo_tiles > 0 && c->prm.kernel == LBM_KERNEL_HALO && (s = build_halo_lists(c))) return s;
   c->has_geometry = true;
   return LBM_OK;
 }

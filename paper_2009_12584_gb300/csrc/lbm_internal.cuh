@@ -55,6 +55,7 @@ struct lbm_ctx {
   int64_t n_tiles;
   bool tile_smem_set;  // k_tile's dynamic shared memory limit raised on this context's device
   bool march_smem_set;  // k_march's (FP64: above 48 KB) likewise
+  bool halo_built;      // the halo lists match the current geometry
   uint32_t tma_extra_tx;  // test hook of the TMA schedule's bounded wait (lbm_debug_tma_expect_extra); 0
   uint16_t* halo_entries; // halo schedule: per-tile lists of region slots (null if unused)
   int* halo_off;       // halo schedule: first entry of each tile, total at [n_halo_tiles]

@@ -115,8 +115,8 @@ def test_tiled_schedule_workspace_without_gpu():
     each 32 x 14 tile plus per-tile offsets and (owned, listed) count pairs,
     each array 256-byte aligned), and for 16-bit storage a third density
     plane pair; the TMA schedule (FP32 only) adds a 16-byte work item per
-    tile; AUTO keeps the tiled lists for 4- and 8-byte storage only; an
-    unknown schedule is rejected."""
+    tile; AUTO keeps the tiled lists (and the halo lists) for 4- and 8-byte
+    storage only; an unknown schedule is rejected."""
     lbm.load()
     align = lambda n: (n + 255) // 256 * 256
     for nx, ny in ((8192, 8192), (100, 70), (4, 4)):
@@ -129,8 +129,12 @@ def test_tiled_schedule_workspace_without_gpu():
             if st == "fp32":
                 tma = lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="tma"))
                 assert tma - tiled == align(nt * 16), (nx, ny)
-            # AUTO runs the tiled schedule for 4- and 8-byte storage
-            assert lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="auto")) == tiled
+            # AUTO keeps the tiled lists and room for the halo lists (4- and
+            # 8-byte storage: tiled under the improved scheme, halo under the
+            # one-node-reach schemes)
+            nh = -(-nx // 32) * -(-ny // 14)
+            halo_extra = align(nh * 38 * 20 * 2) + align((nh + 1) * 4) + align(nh * 16) + align(nh * 24 * 4)
+            assert lbm.workspace_bytes(lbm.make_params(nx, ny, storage=st, kernel="auto")) == tiled + halo_extra
         px = -(-(32 + nx + 4) // 32) * 32  # padded pitch and rows
         plane = px * (ny + 8)
         for st in ("fp16", "bf16"):

@@ -167,6 +167,33 @@ def test_fp64_no_solid_and_isolated_fluid(kernel):
     assert max(errors(o, g, mask)) < 1e-11
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp64"])
+def test_auto_schedule_follows_wetting_scheme(storage):
+    """AUTO runs the halo schedule under the one-node-reach schemes and the
+    tiled one under the improved scheme; switching the scheme mid-run (halo
+    -> tiled -> halo, the density plane recomputed where needed) gives the
+    two-pass schedule's results bit for bit."""
+    nx, ny = 70, 45
+    mask = inputs.random_solid_mask(nx, ny, seed=21, fraction=0.15, periodic_x=True, periodic_y=True)
+    rA, rB, ux, uy = inputs.random_fields(nx, ny, seed=22, lo=0.2, hi=0.9, umax=0.01)
+    plan = [("mc", 9), ("improved", 7), ("llkc", 6), ("constant", 5), ("improved", 4)]
+    out = {}
+    for kernel in ("auto", "two_pass"):
+        sim = lbm.Simulation(nx, ny, periodic_x=True, periodic_y=True, storage=storage, kernel=kernel)
+        sim.set_geometry(mask)
+        for j, (wet, steps) in enumerate(plan):
+            kind, gkw = WETTINGS[wet][1]
+            sim.set_wetting(kind, **gkw)
+            if j == 0:
+                sim.init_fields(rA, rB, ux, uy)
+            sim.step(steps)
+        out[kernel] = [t.cpu() for t in sim.moments()] + [np.asarray(sim.mass())]
+        sim.close()
+    for a, b in zip(out["auto"][:3], out["two_pass"][:3]):
+        assert torch.equal(a, b)
+    assert np.array_equal(out["auto"][3], out["two_pass"][3])
+
+
 @pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16"])
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_no_fluid_node(kernel, storage):
